@@ -1,0 +1,164 @@
+"""CPU oracle for the stable LSD radix sort (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never loads it.
+
+The arithmetic lives in ``rs_oracle.c`` (plain C, compiled here with gcc into
+``liboracle.so``); this module only marshals numpy arrays across ctypes.
+Every function follows the paper's definitions:
+
+* ``digit_histograms`` / ``exclusive_prefix`` -- counting and prefix-sum steps
+  of the naive counting sort (Sec. 3; Alg. 2 ``PrefixSum``).
+* ``counting_pass`` -- one stable counting-sort pass by byte ``p`` (Sec. 3).
+* ``sort_pairs`` / ``sort_keys`` -- LSD radix sort, K = 32, D = 8, four
+  passes (Sec. 4).
+* ``sort_pairs_segmented`` -- the same sort inside every segment (no paper
+  counterpart; plain definition).
+* ``sort_pairs_threaded`` -- same result on several host threads, used to time
+  the CPU baseline.
+
+Every function takes an optional ``lib`` (a library bound by ``_bind``) so that
+the pin tests can also be run against deliberately mutated builds of the C
+source, to show that the pins catch plausible mistakes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rs_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``rs_oracle.c`` into ``liboracle.so`` (gcc, -O2, pthreads)."""
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _bind(path: str):
+    lib = ctypes.CDLL(path)
+    lib.oracle_digit_histograms.argtypes = [_u32p, ctypes.c_size_t, _u64p]
+    lib.oracle_digit_histograms.restype = None
+    lib.oracle_exclusive_prefix.argtypes = [_u64p, _u64p]
+    lib.oracle_exclusive_prefix.restype = None
+    lib.oracle_counting_pass.argtypes = [_u32p, _u32p, _u32p, _u32p,
+                                         ctypes.c_size_t, ctypes.c_uint]
+    lib.oracle_counting_pass.restype = None
+    lib.oracle_sort_pairs.argtypes = [_u32p, _u32p, _u32p, _u32p, ctypes.c_size_t]
+    lib.oracle_sort_pairs.restype = ctypes.c_int
+    lib.oracle_sort_pairs_segmented.argtypes = [_u32p, _u32p, _u32p, _u32p,
+                                                ctypes.c_size_t, _u32p, ctypes.c_uint32]
+    lib.oracle_sort_pairs_segmented.restype = ctypes.c_int
+    lib.oracle_sort_pairs_threaded.argtypes = [_u32p, _u32p, _u32p, _u32p,
+                                               ctypes.c_size_t, ctypes.c_uint]
+    lib.oracle_sort_pairs_threaded.restype = ctypes.c_int
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _bind(build())
+    return _lib
+
+
+def _u32(a) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    if a.dtype != np.uint32:
+        raise TypeError("expected uint32 array, got %s" % a.dtype)
+    return a
+
+
+def _ptr(a, kind=_u32p):
+    return None if a is None else a.ctypes.data_as(kind)
+
+
+def digit_histograms(keys, lib=None) -> np.ndarray:
+    """H[p, b] = number of keys whose byte p equals b; shape (4, 256), uint64."""
+    keys = _u32(keys)
+    h = np.zeros((4, 256), dtype=np.uint64)
+    (lib or _load()).oracle_digit_histograms(_ptr(keys), keys.size, _ptr(h, _u64p))
+    return h
+
+
+def exclusive_prefix(hist, lib=None) -> np.ndarray:
+    """G[p, b] = sum of H[p, b'] over b' < b; shape (4, 256), uint64."""
+    h = np.ascontiguousarray(hist, dtype=np.uint64).reshape(4, 256)
+    g = np.zeros((4, 256), dtype=np.uint64)
+    (lib or _load()).oracle_exclusive_prefix(_ptr(h, _u64p), _ptr(g, _u64p))
+    return g
+
+
+def counting_pass(keys, vals, p: int, lib=None):
+    """One stable counting-sort pass by byte ``p``; returns (keys, vals|None)."""
+    keys = _u32(keys)
+    vals = None if vals is None else _u32(vals)
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    (lib or _load()).oracle_counting_pass(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), keys.size, p)
+    return ko, vo
+
+
+def sort_pairs(keys, vals, lib=None):
+    """Stable ascending LSD radix sort; returns new (keys, vals) arrays."""
+    keys = _u32(keys)
+    vals = None if vals is None else _u32(vals)
+    if vals is not None and vals.size != keys.size:
+        raise ValueError("keys and vals differ in length")
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    rc = (lib or _load()).oracle_sort_pairs(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), keys.size)
+    if rc:
+        raise MemoryError("oracle_sort_pairs failed (%d)" % rc)
+    return ko, vo
+
+
+def sort_keys(keys, lib=None) -> np.ndarray:
+    return sort_pairs(keys, None, lib)[0]
+
+
+def sort_pairs_segmented(keys, vals, offsets, lib=None):
+    """Sort every segment [offsets[s], offsets[s+1]) on its own."""
+    keys = _u32(keys)
+    vals = None if vals is None else _u32(vals)
+    offsets = _u32(offsets)
+    nseg = max(offsets.size - 1, 0)
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    rc = (lib or _load()).oracle_sort_pairs_segmented(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo),
+                                             keys.size, _ptr(offsets), nseg)
+    if rc == -2:
+        raise ValueError("malformed segment table")
+    if rc:
+        raise MemoryError("oracle_sort_pairs_segmented failed (%d)" % rc)
+    return ko, vo
+
+
+def sort_pairs_threaded(keys, vals, nthreads: int, lib=None):
+    """Same result as ``sort_pairs`` computed by ``nthreads`` host threads."""
+    keys = _u32(keys)
+    vals = None if vals is None else _u32(vals)
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    rc = (lib or _load()).oracle_sort_pairs_threaded(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo),
+                                            keys.size, int(nthreads))
+    if rc:
+        raise MemoryError("oracle_sort_pairs_threaded failed (%d)" % rc)
+    return ko, vo

@@ -1,0 +1,226 @@
+/*
+ * rs_oracle.c -- CPU oracle for the stable LSD radix sort of 32-bit unsigned
+ * keys (optionally carrying a 32-bit value) described by Wassenberg & Sanders,
+ * "Faster Radix Sort via Virtual Memory and Write-Combining" (2010).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, calls or
+ * includes this file; only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark load it.  It shares no code, header, table or helper
+ * with the CUDA path.
+ *
+ * What it computes, and from which passage:
+ *   - Problem statement (Abstract; Sec. 1): 32-bit integer keys, optionally
+ *     paired with a 32-bit value.  Keys are read as unsigned and sorted
+ *     ascending; a value is an opaque payload that travels with its key.
+ *   - One pass = the naive counting sort of Sec. 3: histogram of the digit,
+ *     prefix sum to the first output slot of every bucket, then every item in
+ *     input order is written at its bucket's slot, which is post-incremented.
+ *     Visiting items in input order is what makes the pass stable (Sec. 4).
+ *   - The radix sort is the LSD variant of Sec. 4 with K = 32 and D = 8
+ *     (Alg. 2 uses D = 8 so that a digit is a byte): K/D = 4 passes over
+ *     digits 0 (least significant byte) to 3.  Alg. 2 takes digit 3 first
+ *     ("reverse sorting") and then digits 0, 1, 2 inside every MSD bucket;
+ *     both orders yield the same unique stable ascending result, and this
+ *     oracle uses the plain LSD order.
+ *   - Segmented form: the same sort applied to every [off[s], off[s+1]).
+ *     The paper has no segmented case; this is the plain definition.
+ *   - A threaded variant (per-thread chunk histograms, prefix in
+ *     (digit, thread) order, scatter) that yields the identical result; it is
+ *     what the CPU baseline times on all host cores.
+ *
+ * Everything is written as plain loops, with no blocking, fusion or
+ * reordering beyond the counting sort itself.
+ */
+#define _POSIX_C_SOURCE 200809L
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define RADIX_BITS 8u
+#define RADIX 256u
+#define PASSES 4u
+
+/* Digit p of a key: byte p, p = 0 least significant (Alg. 2, Digit()). */
+static uint32_t digit_of(uint32_t key, unsigned p) {
+    return (key >> (RADIX_BITS * p)) & (RADIX - 1u);
+}
+
+/* All four digit histograms: hist[p*256 + b] = #{i : digit_of(keys[i], p) == b}.
+ * Counting step of the naive counting sort (Sec. 3), done for every digit. */
+void oracle_digit_histograms(const uint32_t* keys, size_t n, uint64_t* hist) {
+    memset(hist, 0, sizeof(uint64_t) * RADIX * PASSES);
+    for (size_t i = 0; i < n; ++i)
+        for (unsigned p = 0; p < PASSES; ++p)
+            hist[p * RADIX + digit_of(keys[i], p)] += 1;
+}
+
+/* Exclusive prefix over the buckets of every digit: first output slot of each
+ * bucket (Sec. 3 "prefix sum"; Alg. 2 PrefixSum(bucketSizes)). */
+void oracle_exclusive_prefix(const uint64_t* hist, uint64_t* first) {
+    for (unsigned p = 0; p < PASSES; ++p) {
+        uint64_t run = 0;
+        for (unsigned b = 0; b < RADIX; ++b) {
+            first[p * RADIX + b] = run;
+            run += hist[p * RADIX + b];
+        }
+    }
+}
+
+/* One stable counting-sort pass by digit p (Sec. 3): src -> dst.
+ * vals_src / vals_dst may be NULL for keys only. */
+void oracle_counting_pass(const uint32_t* keys_src, const uint32_t* vals_src,
+                          uint32_t* keys_dst, uint32_t* vals_dst,
+                          size_t n, unsigned p) {
+    uint64_t count[RADIX];
+    uint64_t next[RADIX];
+    memset(count, 0, sizeof(count));
+    for (size_t i = 0; i < n; ++i)
+        count[digit_of(keys_src[i], p)] += 1;
+    uint64_t run = 0;
+    for (unsigned b = 0; b < RADIX; ++b) {
+        next[b] = run;
+        run += count[b];
+    }
+    for (size_t i = 0; i < n; ++i) {
+        uint32_t b = digit_of(keys_src[i], p);
+        uint64_t slot = next[b];
+        next[b] = slot + 1;
+        keys_dst[slot] = keys_src[i];
+        if (vals_src) vals_dst[slot] = vals_src[i];
+    }
+}
+
+/* Full LSD radix sort, passes 0..3 (Sec. 4, K = 32, D = 8).
+ * keys_out / vals_out receive the result; inputs are not modified.
+ * vals_in / vals_out may be NULL (keys only).  Returns 0, or -1 on
+ * allocation failure. */
+int oracle_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in,
+                      uint32_t* keys_out, uint32_t* vals_out, size_t n) {
+    if (n == 0) return 0;
+    uint32_t* ka = (uint32_t*)malloc(n * sizeof(uint32_t));
+    uint32_t* kb = (uint32_t*)malloc(n * sizeof(uint32_t));
+    uint32_t* va = vals_in ? (uint32_t*)malloc(n * sizeof(uint32_t)) : NULL;
+    uint32_t* vb = vals_in ? (uint32_t*)malloc(n * sizeof(uint32_t)) : NULL;
+    if (!ka || !kb || (vals_in && (!va || !vb))) {
+        free(ka); free(kb); free(va); free(vb);
+        return -1;
+    }
+    memcpy(ka, keys_in, n * sizeof(uint32_t));
+    if (vals_in) memcpy(va, vals_in, n * sizeof(uint32_t));
+    for (unsigned p = 0; p < PASSES; ++p) {
+        oracle_counting_pass(ka, va, kb, vb, n, p);
+        uint32_t* t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    memcpy(keys_out, ka, n * sizeof(uint32_t));
+    if (vals_in) memcpy(vals_out, va, n * sizeof(uint32_t));
+    free(ka); free(kb); free(va); free(vb);
+    return 0;
+}
+
+/* Segmented sort: every segment [offsets[s], offsets[s+1]) is sorted on its
+ * own, s = 0..num_segments-1.  offsets has num_segments + 1 nondecreasing
+ * entries; items outside [offsets[0], offsets[S]) are copied unchanged.
+ * Returns 0, -1 on allocation failure, -2 on a malformed table. */
+int oracle_sort_pairs_segmented(const uint32_t* keys_in, const uint32_t* vals_in,
+                                uint32_t* keys_out, uint32_t* vals_out, size_t n,
+                                const uint32_t* offsets, uint32_t num_segments) {
+    for (uint32_t s = 0; s < num_segments; ++s)
+        if (offsets[s] > offsets[s + 1]) return -2;
+    if (num_segments > 0 && offsets[num_segments] > n) return -2;
+    memcpy(keys_out, keys_in, n * sizeof(uint32_t));
+    if (vals_in) memcpy(vals_out, vals_in, n * sizeof(uint32_t));
+    for (uint32_t s = 0; s < num_segments; ++s) {
+        size_t lo = offsets[s], len = (size_t)offsets[s + 1] - offsets[s];
+        int rc = oracle_sort_pairs(keys_in + lo, vals_in ? vals_in + lo : NULL,
+                                   keys_out + lo, vals_out ? vals_out + lo : NULL, len);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Threaded variant (same result).  Thread t owns the contiguous chunk
+ * [t*n/T, (t+1)*n/T).  Per pass: every thread counts its chunk; the first
+ * slot of (bucket b, thread t) is the number of items with a smaller digit
+ * plus the items of bucket b held by threads before t; every thread then
+ * scatters its chunk in input order.  Since chunks are in input order and
+ * slots are assigned in (digit, thread, position) order, the pass is the
+ * same stable counting sort as above.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    size_t lo, hi;                 /* this thread's chunk of the input */
+    pthread_barrier_t* bar;
+    uint64_t* all_counts;          /* [nthreads][RADIX] chunk histograms */
+    unsigned nthreads, tid;
+    uint32_t *ka, *kb, *va, *vb;   /* ping-pong buffers shared by all threads */
+} par_arg;
+
+static void* par_worker(void* vp) {
+    par_arg* a = (par_arg*)vp;
+    uint32_t *ks = a->ka, *kd = a->kb, *vs = a->va, *vd = a->vb;
+    for (unsigned p = 0; p < PASSES; ++p) {
+        uint64_t* mine = a->all_counts + (size_t)a->tid * RADIX;
+        memset(mine, 0, RADIX * sizeof(uint64_t));
+        for (size_t i = a->lo; i < a->hi; ++i) mine[digit_of(ks[i], p)] += 1;
+        pthread_barrier_wait(a->bar);
+        uint64_t next[RADIX];
+        uint64_t run = 0;
+        for (unsigned b = 0; b < RADIX; ++b) {
+            for (unsigned t = 0; t < a->nthreads; ++t) {
+                if (t == a->tid) next[b] = run;
+                run += a->all_counts[(size_t)t * RADIX + b];
+            }
+        }
+        for (size_t i = a->lo; i < a->hi; ++i) {
+            uint32_t b = digit_of(ks[i], p);
+            uint64_t slot = next[b]++;
+            kd[slot] = ks[i];
+            if (vs) vd[slot] = vs[i];
+        }
+        pthread_barrier_wait(a->bar);
+        uint32_t* t = ks; ks = kd; kd = t;
+        t = vs; vs = vd; vd = t;
+    }
+    return NULL;
+}
+
+int oracle_sort_pairs_threaded(const uint32_t* keys_in, const uint32_t* vals_in,
+                               uint32_t* keys_out, uint32_t* vals_out, size_t n,
+                               unsigned nthreads) {
+    if (n == 0) return 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    uint32_t* ka = (uint32_t*)malloc(n * sizeof(uint32_t));
+    uint32_t* kb = (uint32_t*)malloc(n * sizeof(uint32_t));
+    uint32_t* va = vals_in ? (uint32_t*)malloc(n * sizeof(uint32_t)) : NULL;
+    uint32_t* vb = vals_in ? (uint32_t*)malloc(n * sizeof(uint32_t)) : NULL;
+    uint64_t* counts = (uint64_t*)malloc((size_t)nthreads * RADIX * sizeof(uint64_t));
+    par_arg* args = (par_arg*)malloc(nthreads * sizeof(par_arg));
+    pthread_t* th = (pthread_t*)malloc(nthreads * sizeof(pthread_t));
+    if (!ka || !kb || (vals_in && (!va || !vb)) || !counts || !args || !th) {
+        free(ka); free(kb); free(va); free(vb); free(counts); free(args); free(th);
+        return -1;
+    }
+    memcpy(ka, keys_in, n * sizeof(uint32_t));
+    if (vals_in) memcpy(va, vals_in, n * sizeof(uint32_t));
+    pthread_barrier_t bar;
+    pthread_barrier_init(&bar, NULL, nthreads);
+    for (unsigned t = 0; t < nthreads; ++t) {
+        par_arg* a = &args[t];
+        a->lo = (size_t)((unsigned __int128)n * t / nthreads);
+        a->hi = (size_t)((unsigned __int128)n * (t + 1) / nthreads);
+        a->bar = &bar; a->all_counts = counts; a->nthreads = nthreads; a->tid = t;
+        a->ka = ka; a->kb = kb; a->va = va; a->vb = vb;
+    }
+    for (unsigned t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, par_worker, &args[t]);
+    par_worker(&args[0]);
+    for (unsigned t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    pthread_barrier_destroy(&bar);
+    /* PASSES is even, so after the last swap the result is back in ka/va. */
+    memcpy(keys_out, ka, n * sizeof(uint32_t));
+    if (vals_in) memcpy(vals_out, va, n * sizeof(uint32_t));
+    free(ka); free(kb); free(va); free(vb); free(counts); free(args); free(th);
+    return 0;
+}

@@ -1,0 +1,213 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each ``pin_*`` function raises AssertionError when the oracle (the default
+build, or a library bound from a mutated copy of its C source) disagrees with
+something other than itself:
+
+* numpy's stable argsort (a library routine with the same unique answer),
+* the closed-form stable rank  rank(i) = #{j : k_j < k_i} + #{j < i : k_j = k_i}
+  evaluated by brute force on tiny inputs and exhaustively on small alphabets,
+* invariants (nondecreasing, permutation, equal keys keep input order),
+* special cases with known answers (all equal, sorted, reverse sorted),
+* closed-form histograms and prefix sums.
+
+The paper defines a pass as the naive counting sort of Sec. 3, the sort as
+LSD radix with K = 32 and D = 8 (Sec. 4, Alg. 2), and stability as keeping
+the input order of equal keys (Sec. 4).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+import oracle
+from paper_1008_2849_gb300 import inputs
+
+
+def stable_rank_bruteforce(keys):
+    """rank(i) = #{j : k_j < k_i} + #{j < i : k_j == k_i}, by plain loops."""
+    n = len(keys)
+    rank = [0] * n
+    for i in range(n):
+        r = 0
+        for j in range(n):
+            if keys[j] < keys[i] or (keys[j] == keys[i] and j < i):
+                r += 1
+        rank[i] = r
+    return rank
+
+
+def pin_numpy_stable(lib=None):
+    cases = [("uniform", 1), ("uniform", 2), ("uniform", 31), ("uniform", 4097),
+             ("uniform", 100003), ("and2", 65537), ("and4", 50000),
+             ("distinct256", 70001), ("low16", 30011), ("equal", 1000),
+             ("sorted", 5000), ("reverse", 5000)]
+    for dist, n in cases:
+        k = inputs.keys(dist, n, seed=7)
+        v = inputs.index_values(n)
+        ko, vo = oracle.sort_pairs(k, v, lib=lib)
+        perm = np.argsort(k, kind="stable")
+        assert np.array_equal(ko, k[perm]), (dist, n, "keys")
+        assert np.array_equal(vo, v[perm]), (dist, n, "values")
+        kk = oracle.sort_keys(k, lib=lib)
+        assert np.array_equal(kk, k[perm]), (dist, n, "keys only")
+
+
+def pin_bruteforce_tiny(lib=None):
+    rng_keys = [inputs.splitmix32(5, n, 0) for n in (0, 1, 2, 3, 7, 16, 33)]
+    # Small alphabets force many ties, where stability is visible.
+    rng_keys += [inputs.splitmix32(6, 40, 0) & np.uint32(0x03000301)]
+    for k in rng_keys:
+        n = k.size
+        v = inputs.splitmix32(8, n, 1)  # arbitrary payloads
+        ko, vo = oracle.sort_pairs(k, v, lib=lib)
+        rank = stable_rank_bruteforce([int(x) for x in k])
+        exp_k = np.empty_like(k)
+        exp_v = np.empty_like(v)
+        for i in range(n):
+            exp_k[rank[i]] = k[i]
+            exp_v[rank[i]] = v[i]
+        assert np.array_equal(ko, exp_k), ("keys", n)
+        assert np.array_equal(vo, exp_v), ("values", n)
+
+
+# Four-symbol alphabets: each puts its order into different bytes, so a pass
+# that is dropped, reordered or mis-shifted, or a signed reading, shows up.
+ALPHABETS = (
+    (0x00000001, 0x00000100, 0x00010000, 0x01000000),
+    (0xFF000000, 0x00FFFFFF, 0x80000000, 0x7FFFFFFF),
+    (0x00000102, 0x00000201, 0x00000101, 0x00000202),
+    (0x01FF00FF, 0x0100FF00, 0x00FFFF00, 0x0000FFFF),
+)
+
+
+def pin_exhaustive_small(lib=None, max_len=6):
+    """Every sequence of length <= max_len over each alphabet, as segments."""
+    for alpha in ALPHABETS:
+        seqs = []
+        for L in range(0, max_len + 1):
+            seqs.extend(itertools.product(range(4), repeat=L))
+        sizes = np.array([len(s) for s in seqs], dtype=np.uint64)
+        off = inputs.offsets_from_sizes(sizes)
+        sym = np.fromiter(itertools.chain.from_iterable(seqs), dtype=np.int64,
+                          count=int(off[-1]))
+        k = np.asarray(alpha, dtype=np.uint32)[sym]
+        v = np.arange(k.size, dtype=np.uint32)
+        ko, vo = oracle.sort_pairs_segmented(k, v, off, lib=lib)
+        # Expected: per segment, stable rank by the closed form, vectorised
+        # over all segments of one length at a time.
+        for L in range(1, max_len + 1):
+            idx = np.nonzero(sizes == L)[0]
+            starts = off[idx].astype(np.int64)
+            cols = starts[:, None] + np.arange(L)[None, :]
+            kk = k[cols].astype(np.int64)                    # (S, L)
+            less = (kk[:, None, :] < kk[:, :, None]).sum(axis=2)
+            tri = np.tril(np.ones((L, L), dtype=bool), -1)   # j < i
+            eq_before = ((kk[:, None, :] == kk[:, :, None]) & tri[None]).sum(axis=2)
+            rank = less + eq_before                          # (S, L)
+            exp_k = np.empty_like(kk)
+            exp_v = np.empty_like(kk)
+            rows = np.arange(len(idx))[:, None]
+            exp_k[rows, rank] = kk
+            exp_v[rows, rank] = cols
+            assert np.array_equal(ko[cols].astype(np.int64), exp_k), (alpha, L, "keys")
+            assert np.array_equal(vo[cols].astype(np.int64), exp_v), (alpha, L, "values")
+
+
+def pin_invariants(lib=None):
+    for dist in inputs.DISTRIBUTIONS:
+        n = 20011
+        k = inputs.keys(dist, n, seed=11)
+        v = inputs.index_values(n)
+        ko, vo = oracle.sort_pairs(k, v, lib=lib)
+        assert np.all(ko[1:] >= ko[:-1]), (dist, "nondecreasing")
+        assert np.array_equal(np.sort(vo), v), (dist, "values form a permutation")
+        assert np.array_equal(k[vo], ko), (dist, "each key travels with its value")
+        same = ko[1:] == ko[:-1]
+        assert np.all(vo[1:][same] > vo[:-1][same]), (dist, "stable")
+
+
+def pin_special_cases(lib=None):
+    n = 9999
+    v = inputs.index_values(n)
+    # All keys equal: identity permutation.
+    ko, vo = oracle.sort_pairs(inputs.keys("equal", n, 3), v, lib=lib)
+    assert np.array_equal(vo, v)
+    # Already sorted: identity permutation.
+    k = inputs.keys("sorted", n, 4)
+    ko, vo = oracle.sort_pairs(k, v, lib=lib)
+    assert np.array_equal(vo, v) and np.array_equal(ko, k)
+    # Reverse sorted with distinct keys: the permutation is the reversal.
+    k = np.arange(n, 0, -1, dtype=np.uint32) * np.uint32(429497)
+    ko, vo = oracle.sort_pairs(k, v, lib=lib)
+    assert np.array_equal(vo, v[::-1]) and np.array_equal(ko, k[::-1])
+    # Keys 0..n-1 in a fixed shuffled order come out as 0..n-1.
+    perm = np.argsort(inputs.splitmix32(9, n, 0), kind="stable").astype(np.uint32)
+    ko, vo = oracle.sort_pairs(perm, v, lib=lib)
+    assert np.array_equal(ko, v) and np.array_equal(perm[vo], v)
+    # Top bit set sorts after top bit clear (unsigned keys, Abstract / Sec. 1).
+    k = np.array([0x80000000, 0x7FFFFFFF, 0xFFFFFFFF, 0], dtype=np.uint32)
+    ko, _ = oracle.sort_pairs(k, None, lib=lib)
+    assert ko.tolist() == [0, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFF]
+
+
+def pin_histograms(lib=None):
+    # Keys 0..65535: bytes 0 and 1 take every value 256 times, bytes 2 and 3
+    # are always zero.
+    k = np.arange(65536, dtype=np.uint32)
+    h = oracle.digit_histograms(k, lib=lib)
+    assert np.all(h[0] == 256) and np.all(h[1] == 256)
+    assert h[2, 0] == 65536 and h[2, 1:].sum() == 0
+    assert h[3, 0] == 65536 and h[3, 1:].sum() == 0
+    # Against numpy's bincount of each byte.
+    k = inputs.keys("and2", 54321, 12)
+    h = oracle.digit_histograms(k, lib=lib)
+    for p in range(4):
+        ref = np.bincount((k >> np.uint32(8 * p)) & np.uint32(255), minlength=256)
+        assert np.array_equal(h[p], ref.astype(np.uint64)), p
+    # Prefix: closed form on flat counts, and numpy's cumsum otherwise.
+    g = oracle.exclusive_prefix(np.full((4, 256), 3, dtype=np.uint64), lib=lib)
+    assert np.array_equal(g, np.tile(np.arange(256, dtype=np.uint64) * 3, (4, 1)))
+    g = oracle.exclusive_prefix(h, lib=lib)
+    ref = np.concatenate([np.zeros((4, 1), dtype=np.uint64), np.cumsum(h, axis=1)[:, :-1]], axis=1)
+    assert np.array_equal(g, ref)
+
+
+def pin_counting_pass(lib=None):
+    k = inputs.keys("uniform", 30001, 13)
+    v = inputs.index_values(k.size)
+    for p in range(4):
+        ko, vo = oracle.counting_pass(k, v, p, lib=lib)
+        d = (k >> np.uint32(8 * p)) & np.uint32(255)
+        perm = np.argsort(d, kind="stable")
+        assert np.array_equal(ko, k[perm]) and np.array_equal(vo, v[perm]), p
+
+
+def pin_segmented(lib=None):
+    sizes = np.array([0, 1, 5, 0, 300, 1, 4096, 2, 0, 777], dtype=np.uint64)
+    off = inputs.offsets_from_sizes(sizes)
+    n = int(off[-1])
+    k = inputs.keys("and2", n, 14)
+    v = inputs.index_values(n)
+    ko, vo = oracle.sort_pairs_segmented(k, v, off, lib=lib)
+    for s in range(sizes.size):
+        a, b = int(off[s]), int(off[s + 1])
+        perm = np.argsort(k[a:b], kind="stable")
+        assert np.array_equal(ko[a:b], k[a:b][perm]), s
+        assert np.array_equal(vo[a:b], v[a:b][perm]), s
+
+
+def pin_threaded(lib=None):
+    for n in (1, 3, 1000, 65537):
+        k = inputs.keys("and3", n, 15)
+        v = inputs.index_values(n)
+        ref_k, ref_v = oracle.sort_pairs(k, v, lib=lib)
+        for t in (1, 2, 3, 8):
+            ko, vo = oracle.sort_pairs_threaded(k, v, t, lib=lib)
+            assert np.array_equal(ko, ref_k) and np.array_equal(vo, ref_v), (n, t)
+
+
+ALL_PINS = (pin_numpy_stable, pin_bruteforce_tiny, pin_exhaustive_small, pin_invariants,
+            pin_special_cases, pin_histograms, pin_counting_pass, pin_segmented,
+            pin_threaded)
