@@ -1,0 +1,299 @@
+"""Benchmark of the GB300 radix sort.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete sort (digit histograms, prefix/plan, four scatter
+passes) of 2^28 (uint32 key, uint32 value = index) pairs with uniform keys
+(seed 2), through the C ABI call rs_sort_pairs_ex on the current stream.
+Every step sorts its own freshly copied input (2 GiB, far larger than the
+129 MB L2), so no step sees data left in cache by the previous one.
+
+Printed (rank 0, one JSON line): pairs/s for the whole job; the dominant
+kernel's achieved HBM bandwidth against the measured copy peak (roofline);
+the same metric end to end through rs_sort_pairs_host with pinned host
+buffers (copies included); the CPU oracle's throughput on a bounded sample
+(cpu_baseline); SM clocks sampled during the timed region.
+
+With N > 1 (torchrun), every rank sorts its own independent 2^28-pair array
+(replicas: the sort of one array does not shard without an exchange step),
+the time is the maximum over ranks, and the value counts all ranks' pairs.
+
+--impl reference times the CPU oracle (the plain LSD counting sort of the
+paper's Sec. 3/4, run on all host cores) on a bounded sample of the same
+workload; there is no GPU in that arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1008_2849_gb300 import inputs, roofline  # noqa: E402
+
+METRIC = "32-bit key-value pairs sorted/s"
+UNIT = "pairs/s"
+N_PAIRS = 1 << 28
+KEY_SEED = 2
+WORKLOAD = "sort_pairs_u32_2^28_uniform"
+ONESWEEP_SOURCES = ("paper_1008_2849_gb300/csrc/rs_onesweep.cuh",
+                    "paper_1008_2849_gb300/csrc/rs_onesweep_launch.cuh",
+                    "paper_1008_2849_gb300/csrc/rs_device.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pairs_2^28_traffic.txt")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def source_hash(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the scatter kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    try:
+        vals = {}
+        for line in open(TRAFFIC_FILE):
+            line = line.split("#", 1)[0].strip()
+            if "=" in line:
+                k, v = line.split("=", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("source_hash") != source_hash(ONESWEEP_SOURCES):
+            return None
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+def cpu_oracle_rate(seconds_budget: float = 12.0, n_sample: int = 1 << 25):
+    """Time the CPU oracle (threaded, all host cores) on a bounded sample of
+    the workload: 2^25 uniform pairs (seed 2), value = index."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    k = inputs.keys("uniform", n_sample, seed=KEY_SEED)
+    v = inputs.index_values(n_sample)
+    rates = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.sort_pairs_threaded(k, v, threads)
+        dt = time.perf_counter() - t0
+        rates.append(n_sample / dt)
+        if time.perf_counter() - t_start > seconds_budget or len(rates) >= 5:
+            break
+    return {"value": statistics.median(rates), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d sorts of 2^25 uniform uint32 pairs (value = index), threaded LSD "
+                      "counting-sort oracle, median" % len(rates)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n_sample = 1 << 24
+    k = inputs.keys("uniform", n_sample, seed=KEY_SEED)
+    v = inputs.index_values(n_sample)
+    for _ in range(args.warmup):
+        oracle.sort_pairs_threaded(k, v, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sort_pairs_threaded(k, v, threads)
+    dt = time.perf_counter() - t0
+    value = args.steps * n_sample / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_PAIRS, "key_dist": "uniform", "seed": KEY_SEED,
+                   "values": "index", "reference_sample_n": n_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "each step sorts 2^24 of the workload's pairs on the host "
+                                   "(threaded LSD counting-sort oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3  # at least three untimed warm-up steps
+
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1008_2849_gb300 import build, clocks, rs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build_library()
+    rs.lib()
+
+    n = N_PAIRS
+    seed = KEY_SEED + 1000 * rank  # every rank sorts an independent array
+    k_host = inputs.keys("uniform", n, seed=seed)
+    v_host = inputs.index_values(n)
+    dev = torch.device("cuda", local)
+    k_src = torch.from_numpy(k_host.view(np.int32)).to(dev)
+    v_src = torch.from_numpy(v_host.view(np.int32)).to(dev)
+
+    total = args.warmup + args.steps
+    bufs = []
+    for _ in range(total):
+        kb = torch.empty_like(k_src)
+        vb = torch.empty_like(v_src)
+        kb.copy_(k_src)
+        vb.copy_(v_src)
+        bufs.append((kb, vb))
+    ws = rs.alloc_workspace(n, True, device=dev)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        rs.sort_pairs_ex(bufs[i][0], bufs[i][1], ws, stream=stream)
+    rs.check_stream(stream)
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = rs.launch_count()
+    rs.profile_enable(True)
+    with clocks.ClockSampler(local) as sampler:
+        ev0.record(stream)
+        for i in range(args.warmup, total):
+            rs.sort_pairs_ex(bufs[i][0], bufs[i][1], ws, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    per_kind = rs.profile_read()
+    rs.profile_enable(False)
+    launches = rs.launch_count() - launches0
+    rs.check_stream(stream)
+    elapsed_ms = ev0.elapsed_time(ev1)
+
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    value = world * args.steps * n / (elapsed_ms / 1e3)
+
+    # Roofline of the dominant kernel: the scatter pass.
+    peaks, peak_src = measured_peaks()
+    os_launches, os_ms = per_kind.get("onesweep", (0, 0.0))
+    hist_launches, hist_ms = per_kind.get("hist4", (0, 0.0))
+    algo_bytes = roofline.scatter_bytes_per_item(True) * n   # per scatter launch
+    achieved = algo_bytes / (os_ms / os_launches / 1e3) / 1e9 if os_launches else None
+    peak = float(peaks["hbm_gbs"])
+    traffic = recorded_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "kernel": "k_onesweep<512,16,pairs>", "peak_source": peak_src + " (hbm_gbs, copy)",
+            "avg_launch_ms": os_ms / os_launches if os_launches else None,
+            "algorithmic_bytes_per_launch": algo_bytes,
+            "hist_avg_launch_ms": hist_ms / hist_launches if hist_launches else None,
+            "hist_achieved_gbs": (roofline.histogram_bytes_per_item() * n / (hist_ms / hist_launches / 1e3) / 1e9)
+            if hist_launches else None,
+            "whole_sort_gbs": roofline.sort_bytes_per_item(True) * n * args.steps / (elapsed_ms / 1e3) / 1e9,
+            "per_kind_ms": {k: v[1] / max(v[0], 1) for k, v in per_kind.items() if v[0]}}
+
+    # Release the step buffers before the end-to-end and CPU legs.
+    del bufs
+    torch.cuda.empty_cache()
+
+    e2e = None
+    if not args.no_e2e:
+        kin = torch.from_numpy(k_host.view(np.int32)).pin_memory()
+        vin = torch.from_numpy(v_host.view(np.int32)).pin_memory()
+        kout = torch.empty_like(kin).pin_memory()
+        vout = torch.empty_like(vin).pin_memory()
+        for _ in range(2):
+            rs.sort_pairs_host(kin, vin, kout, vout)
+        e2e_steps = max(3, min(args.steps, 10))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            rs.sort_pairs_host(kin, vin, kout, vout)
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+        e2e = {"value": world * e2e_steps * n / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+               "api": "rs_sort_pairs_host (pinned host buffers)", "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate()
+
+    if rank == 0:
+        cs = sampler.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "key_dist": "uniform", "seed": KEY_SEED,
+                       "values": "index", "passes": 4, "digit_bits": 8,
+                       "l2": "inputs larger than L2: every step sorts its own fresh 2 GiB copy",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"],
+                       "reasons": cs["reasons"], "samples": cs["samples"], "source": cs["source"]},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

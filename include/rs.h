@@ -1,0 +1,144 @@
+/*
+ * rs.h -- C ABI of librs.so: stable ascending LSD radix sort of 32-bit
+ * unsigned keys, optionally carrying 32-bit values, on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * The operation is the one stated by Wassenberg & Sanders, "Faster Radix
+ * Sort via Virtual Memory and Write-Combining" (2010): 32-bit integer keys,
+ * optionally paired with a 32-bit value (Abstract; Sec. 1), sorted by an LSD
+ * radix sort whose every pass is a stable counting sort -- digit histogram,
+ * prefix sum over buckets, scatter in input order (Sec. 3; Sec. 4, Alg. 2
+ * with K = 32 and D = 8, i.e. four byte-wide passes).  Keys are unsigned and
+ * sorted ascending; equal keys keep their input order (stability, Sec. 4), so
+ * the result is unique: item i goes to position
+ *     #{j : k_j < k_i} + #{j < i : k_j = k_i}.
+ * A value is an opaque payload that moves with its key and is never compared.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named d_* are DEVICE pointers (cudaMalloc'd, managed or
+ *    otherwise GPU-addressable), owned by the caller and never freed here.
+ *    Pointers named h_* are HOST pointers (pinned memory gives full link
+ *    bandwidth; pageable memory works but is slower).
+ *  - Arrays are dense uint32_t, 4-byte aligned; no other alignment is needed.
+ *    Keys and values must not overlap each other or the workspace.
+ *  - Sorting is in place: the sorted keys (and values) replace the input.
+ *  - n counts items (keys), 0 <= n < 2^32.  n = 0 is a no-op returning RS_OK.
+ *  - Argument errors are detected on the host before anything is enqueued and
+ *    returned synchronously (RS_ERR_INVALID_ARG / RS_ERR_UNSUPPORTED).
+ *  - Errors found on the device (a look-back wait that ran out, a position
+ *    outside the array, a malformed segment table) are recorded in a sticky
+ *    device status word.  The plain entry points synchronise and report it;
+ *    the _ex entry points are asynchronous and the caller collects it with
+ *    rs_stream_status().  After a device-side error the contents of the
+ *    caller's arrays are unspecified, but the CUDA context stays usable.
+ *  - The plain entry points use the current device, the legacy default
+ *    stream and a workspace cached inside the library (allocated on first
+ *    use, grown when needed, kept until exit); they serialise on an internal
+ *    lock and return after the sort has completed.
+ *  - The _ex entry points take a stream (cudaStream_t passed as void*, NULL =
+ *    legacy default stream) and a caller-owned device workspace of at least
+ *    rs_workspace_bytes(...) bytes, 256-byte aligned.  They allocate nothing,
+ *    do not synchronise, and return once the work is enqueued.  Two calls in
+ *    flight at the same time must not share a workspace.
+ */
+#ifndef RS_H_
+#define RS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rs_status {
+    RS_OK = 0,
+    RS_ERR_INVALID_ARG = 1,   /* null pointer with n > 0, n >= 2^32, bad table, ... */
+    RS_ERR_OUT_OF_MEMORY = 2, /* device allocation failed (plain calls only) */
+    RS_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    RS_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
+    RS_ERR_UNSUPPORTED = 5,   /* no sm_103a device, or a size this build rejects */
+    RS_ERR_BOUNDS = 6,        /* a kernel's own bounds check refused a write */
+    RS_ERR_BAD_SEGMENTS = 7   /* segment table not monotone or not ending at n */
+} rs_status;
+
+/* Sort n keys in place, ascending (Sec. 4 LSD radix sort, keys only, V = 0
+ * in Table 1).  Synchronous. */
+rs_status rs_sort_keys(uint32_t* d_keys, size_t n);
+
+/* Sort n (key, value) pairs in place by key, ascending and stable (Sec. 4;
+ * K = 32, V = 32 in Table 1).  d_vals[i] travels with d_keys[i].
+ * Synchronous. */
+rs_status rs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, size_t n);
+
+/* Asynchronous forms on a caller stream with a caller workspace.
+ * workspace_bytes must be >= rs_workspace_bytes(n, with_values, 0). */
+rs_status rs_sort_keys_ex(uint32_t* d_keys, size_t n,
+                          void* cuda_stream, void* d_workspace, size_t workspace_bytes);
+rs_status rs_sort_pairs_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                           void* cuda_stream, void* d_workspace, size_t workspace_bytes);
+
+/* Bytes of device workspace an _ex call needs.  n = total items; with_values
+ * = 0 for keys only, 1 for pairs; num_segments = 0 for the unsegmented calls,
+ * else the number of segments of a segmented call.  Pure host arithmetic. */
+size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments);
+
+/* Synchronise cuda_stream (NULL = legacy default stream), then return and
+ * clear the sticky device status word of the current device: RS_OK, or the
+ * first device-side error recorded since the last call (RS_ERR_TIMEOUT,
+ * RS_ERR_BOUNDS, RS_ERR_BAD_SEGMENTS), or RS_ERR_CUDA if the synchronisation
+ * itself failed.  The word is shared by every stream of the device. */
+rs_status rs_stream_status(void* cuda_stream);
+
+/* Static, human-readable name of a status code.  Never NULL. */
+const char* rs_status_string(rs_status status);
+
+/* Digit histograms of n keys (counting step of Sec. 3 for all four digits at
+ * once): d_hist[p*256 + b] = #{i : byte p of d_keys[i] == b}, p = 0..3,
+ * b = 0..255.  d_hist is caller-owned device memory of 1024 uint32_t; it is
+ * overwritten.  Asynchronous on cuda_stream; allocates nothing. */
+rs_status rs_digit_histograms_ex(const uint32_t* d_keys, size_t n, uint32_t* d_hist,
+                                 void* cuda_stream);
+
+/* End-to-end sort of HOST arrays: copies h_keys_in (and h_vals_in, if not
+ * NULL) to the device, sorts, and copies the result to h_keys_out (and
+ * h_vals_out).  Inputs are not modified; output and input may be the same
+ * array.  Device buffers are cached inside the library.  Synchronous. */
+rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in,
+                             uint32_t* h_keys_out, uint32_t* h_vals_out, size_t n);
+
+/* ---- instrumentation (used by the benchmark; off by default) ---------- */
+
+/* Number of kernels this library has launched on any device since it was
+ * loaded (cudaMemset and copies are not counted). */
+uint64_t rs_launch_count(void);
+
+/* on = 1: from now on, bracket every kernel launch with CUDA events on the
+ * launching stream; on = 0: stop and discard recorded events. */
+rs_status rs_profile_enable(int on);
+
+/* Synchronise the recorded events and return, per kernel kind k =
+ * 0..max_kinds-1, the number of launches and their summed device time in
+ * milliseconds since rs_profile_enable(1) or the last rs_profile_read.
+ * Returns the number of kinds (see rs_kernel_kind_name); resets the tallies. */
+int rs_profile_read(uint64_t* launches, double* total_ms, int max_kinds);
+
+/* Name of kernel kind k, or NULL past the last kind. */
+const char* rs_kernel_kind_name(int kind);
+
+/* ---- fault-injection knobs for tests (host-side settings) ------------- */
+
+/* Iteration limit of every look-back wait (0 restores the default). */
+rs_status rs_debug_set_spin_limit(uint32_t iterations);
+
+/* withhold = 1: the first tile of every scatter pass never publishes its
+ * counts, so the waits of the tiles after it run out and the call reports
+ * RS_ERR_TIMEOUT.  0 restores normal operation. */
+rs_status rs_debug_withhold_first_tile(int withhold);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H_ */

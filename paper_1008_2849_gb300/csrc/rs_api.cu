@@ -1,0 +1,367 @@
+// rs_api.cu -- the extern "C" entry points of librs.so (declared in
+// include/rs.h): argument checks, workspace handling for the plain calls,
+// the host-buffer path, the sticky device status word, launch counting and
+// optional per-kernel event timing.
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "rs_device.cuh"
+#include "rs_internal.h"
+
+// Sticky status word, one instance per device (a __device__ variable exists
+// once in every device's copy of the module).  Host code reaches it only
+// through the address cudaGetSymbolAddress returns for the current device.
+static __device__ uint32_t g_rs_sticky_err;
+
+namespace rs {
+
+namespace {
+
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;
+constexpr int kMaxDevices = 64;
+
+std::atomic<uint64_t> g_launches{0};
+
+struct DevState {
+    bool ready = false;
+    DeviceInfo info{};
+    // cached workspace of the plain calls
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // cached device buffers and streams of the host-buffer path
+    uint32_t* hk = nullptr;
+    uint32_t* hv = nullptr;
+    size_t h_cap = 0;
+    cudaStream_t s_main = nullptr, s_side = nullptr;
+    cudaEvent_t ev_vals = nullptr, ev_sorted = nullptr, ev_side_done = nullptr;
+};
+DevState g_dev[kMaxDevices];
+std::mutex g_mu;       // guards the buffers of g_dev and serialises the plain calls
+std::mutex g_info_mu;  // guards g_dev[].ready / .info
+
+// Event timing of launches (benchmark instrumentation).
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_recs;
+std::vector<cudaEvent_t> g_event_pool;
+thread_local cudaEvent_t t_pending_begin = nullptr;
+
+cudaEvent_t pool_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int current_device() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    return dev;
+}
+
+rs_status device_info_for(int dev, DeviceInfo* out) {
+    std::lock_guard<std::mutex> lock(g_info_mu);
+    DevState& d = g_dev[dev];
+    if (!d.ready) {
+        int major = 0, minor = 0, sms = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return RS_ERR_CUDA;
+        if (major != 10 || minor != 3) return RS_ERR_UNSUPPORTED;  // built for sm_103a only
+        void* sticky = nullptr;
+        if (cudaGetSymbolAddress(&sticky, g_rs_sticky_err) != cudaSuccess) return RS_ERR_CUDA;
+        d.info.sm_count = sms;
+        d.info.sticky = static_cast<uint32_t*>(sticky);
+        d.ready = true;
+    }
+    *out = d.info;
+    return RS_OK;
+}
+
+rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n) {
+    if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
+    if (n > 0 && keys == nullptr) return RS_ERR_INVALID_ARG;
+    if (vals != nullptr && n > 0) {
+        const uintptr_t k0 = (uintptr_t)keys, k1 = k0 + n * 4;
+        const uintptr_t v0 = (uintptr_t)vals, v1 = v0 + n * 4;
+        if (k0 < v1 && v0 < k1) return RS_ERR_INVALID_ARG;  // overlapping
+    }
+    if (((uintptr_t)keys & 3u) || ((uintptr_t)vals & 3u)) return RS_ERR_INVALID_ARG;
+    return RS_OK;
+}
+
+rs_status ensure_workspace_locked(DevState& d, size_t bytes) {
+    if (d.ws_bytes >= bytes) return RS_OK;
+    if (d.ws) cudaFree(d.ws);
+    d.ws = nullptr;
+    d.ws_bytes = 0;
+    if (cudaMalloc(&d.ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RS_ERR_OUT_OF_MEMORY;
+    }
+    d.ws_bytes = bytes;
+    return RS_OK;
+}
+
+rs_status sticky_status(cudaStream_t stream) {
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return RS_ERR_CUDA;
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
+    uint32_t bits = 0;
+    if (cudaMemcpy(&bits, di.sticky, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return RS_ERR_CUDA;
+    if (bits) {
+        const uint32_t zero = 0;
+        if (cudaMemcpy(di.sticky, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+            return RS_ERR_CUDA;
+    }
+    if (bits & ERR_TIMEOUT) return RS_ERR_TIMEOUT;
+    if (bits & ERR_SEGMENTS) return RS_ERR_BAD_SEGMENTS;
+    if (bits & ERR_BOUNDS) return RS_ERR_BOUNDS;
+    return RS_OK;
+}
+
+rs_status plain_sort(uint32_t* keys, uint32_t* vals, size_t n) {
+    rs_status st = check_sort_args(keys, vals, n);
+    if (st != RS_OK || n == 0) return st;
+    std::lock_guard<std::mutex> lock(g_mu);
+    const int dev = current_device();
+    if (dev < 0) return RS_ERR_CUDA;
+    DeviceInfo di;
+    st = device_info_for(dev, &di);
+    if (st != RS_OK) return st;
+    DevState& d = g_dev[dev];
+    st = ensure_workspace_locked(d, layout_for(n, vals != nullptr).total);
+    if (st != RS_OK) return st;
+    st = enqueue_sort(keys, vals, (uint32_t)n, cudaStreamLegacy, d.ws, d.ws_bytes);
+    if (st != RS_OK) return st;
+    return sticky_status(cudaStreamLegacy);
+}
+
+}  // namespace
+
+Knobs& knobs() {
+    static Knobs k{1, 1, kDefaultSpinLimit, 0, 4};
+    return k;
+}
+
+const char* kernel_kind_name(int kind) {
+    switch (kind) {
+    case KK_HIST: return "hist4";
+    case KK_PLAN: return "plan";
+    case KK_ONESWEEP: return "onesweep";
+    default: return nullptr;
+    }
+}
+
+rs_status device_info(DeviceInfo* out) {
+    const int dev = current_device();
+    if (dev < 0) return RS_ERR_CUDA;
+    return device_info_for(dev, out);
+}
+
+void note_launch_begin(int kind, cudaStream_t stream) {
+    (void)kind;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    if (!g_prof_on) return;
+    t_pending_begin = pool_event();
+    cudaEventRecord(t_pending_begin, stream);
+}
+
+void note_launch_end(int kind, cudaStream_t stream) {
+    if (t_pending_begin == nullptr) return;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    cudaEvent_t b = pool_event();
+    cudaEventRecord(b, stream);
+    g_prof_recs.push_back(ProfRec{kind, t_pending_begin, b});
+    t_pending_begin = nullptr;
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+rs_status rs_sort_keys(uint32_t* d_keys, size_t n) { return plain_sort(d_keys, nullptr, n); }
+
+rs_status rs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, size_t n) {
+    if (n > 0 && d_vals == nullptr) return RS_ERR_INVALID_ARG;
+    return plain_sort(d_keys, d_vals, n);
+}
+
+static rs_status ex_sort(uint32_t* keys, uint32_t* vals, size_t n, void* stream, void* ws,
+                         size_t ws_bytes) {
+    rs_status st = check_sort_args(keys, vals, n);
+    if (st != RS_OK || n == 0) return st;
+    if (ws_bytes < layout_for(n, vals != nullptr).total || ws == nullptr) return RS_ERR_INVALID_ARG;
+    return enqueue_sort(keys, vals, (uint32_t)n, static_cast<cudaStream_t>(stream), ws, ws_bytes);
+}
+
+rs_status rs_sort_keys_ex(uint32_t* d_keys, size_t n, void* cuda_stream, void* d_workspace,
+                          size_t workspace_bytes) {
+    return ex_sort(d_keys, nullptr, n, cuda_stream, d_workspace, workspace_bytes);
+}
+
+rs_status rs_sort_pairs_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n, void* cuda_stream,
+                           void* d_workspace, size_t workspace_bytes) {
+    if (n > 0 && d_vals == nullptr) return RS_ERR_INVALID_ARG;
+    return ex_sort(d_keys, d_vals, n, cuda_stream, d_workspace, workspace_bytes);
+}
+
+size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments) {
+    (void)num_segments;
+    if (n == 0) return 0;
+    return layout_for(n, with_values != 0).total;
+}
+
+rs_status rs_stream_status(void* cuda_stream) {
+    return sticky_status(static_cast<cudaStream_t>(cuda_stream));
+}
+
+const char* rs_status_string(rs_status status) {
+    switch (status) {
+    case RS_OK: return "ok";
+    case RS_ERR_INVALID_ARG: return "invalid argument";
+    case RS_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case RS_ERR_CUDA: return "CUDA runtime error";
+    case RS_ERR_TIMEOUT: return "device-side wait timed out";
+    case RS_ERR_UNSUPPORTED: return "unsupported device or size";
+    case RS_ERR_BOUNDS: return "device-side bounds check refused a write";
+    case RS_ERR_BAD_SEGMENTS: return "malformed segment table";
+    default: return "unknown status";
+    }
+}
+
+rs_status rs_digit_histograms_ex(const uint32_t* d_keys, size_t n, uint32_t* d_hist,
+                                 void* cuda_stream) {
+    if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
+    if (d_hist == nullptr || (n > 0 && d_keys == nullptr)) return RS_ERR_INVALID_ARG;
+    if (((uintptr_t)d_keys & 3u) || ((uintptr_t)d_hist & 3u)) return RS_ERR_INVALID_ARG;
+    return enqueue_histograms(d_keys, (uint32_t)n, d_hist, static_cast<cudaStream_t>(cuda_stream));
+}
+
+rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in,
+                             uint32_t* h_keys_out, uint32_t* h_vals_out, size_t n) {
+    if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
+    if (n == 0) return RS_OK;
+    if (!h_keys_in || !h_keys_out || (h_vals_in && !h_vals_out)) return RS_ERR_INVALID_ARG;
+    const bool pairs = h_vals_in != nullptr;
+    std::lock_guard<std::mutex> lock(g_mu);
+    const int dev = current_device();
+    if (dev < 0) return RS_ERR_CUDA;
+    DeviceInfo di;
+    rs_status st = device_info_for(dev, &di);
+    if (st != RS_OK) return st;
+    DevState& d = g_dev[dev];
+    if (!d.s_main) {
+        if (cudaStreamCreateWithFlags(&d.s_main, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&d.s_side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d.ev_vals, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d.ev_sorted, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d.ev_side_done, cudaEventDisableTiming) != cudaSuccess)
+            return RS_ERR_CUDA;
+    }
+    if (d.h_cap < n) {
+        if (d.hk) cudaFree(d.hk);
+        if (d.hv) cudaFree(d.hv);
+        d.hk = d.hv = nullptr;
+        d.h_cap = 0;
+        if (cudaMalloc(&d.hk, n * 4) != cudaSuccess || cudaMalloc(&d.hv, n * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return RS_ERR_OUT_OF_MEMORY;
+        }
+        d.h_cap = n;
+    }
+    st = ensure_workspace_locked(d, layout_for(n, pairs).total);
+    if (st != RS_OK) return st;
+    const size_t bytes = n * 4;
+    // Keys first on the main stream (the histogram needs them); values on
+    // the side stream, overlapping the histogram and plan kernels.
+    if (cudaMemcpyAsync(d.hk, h_keys_in, bytes, cudaMemcpyHostToDevice, d.s_main) != cudaSuccess)
+        return RS_ERR_CUDA;
+    if (pairs) {
+        if (cudaMemcpyAsync(d.hv, h_vals_in, bytes, cudaMemcpyHostToDevice, d.s_side) != cudaSuccess ||
+            cudaEventRecord(d.ev_vals, d.s_side) != cudaSuccess ||
+            cudaStreamWaitEvent(d.s_main, d.ev_vals, 0) != cudaSuccess)
+            return RS_ERR_CUDA;
+    }
+    st = enqueue_sort(d.hk, pairs ? d.hv : nullptr, (uint32_t)n, d.s_main, d.ws, d.ws_bytes);
+    if (st != RS_OK) return st;
+    if (pairs) {
+        if (cudaEventRecord(d.ev_sorted, d.s_main) != cudaSuccess ||
+            cudaStreamWaitEvent(d.s_side, d.ev_sorted, 0) != cudaSuccess ||
+            cudaMemcpyAsync(h_vals_out, d.hv, bytes, cudaMemcpyDeviceToHost, d.s_side) != cudaSuccess)
+            return RS_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(h_keys_out, d.hk, bytes, cudaMemcpyDeviceToHost, d.s_main) != cudaSuccess)
+        return RS_ERR_CUDA;
+    if (cudaStreamSynchronize(d.s_side) != cudaSuccess) return RS_ERR_CUDA;
+    return sticky_status(d.s_main);
+}
+
+uint64_t rs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rs_status rs_profile_enable(int on) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_prof_on = on != 0;
+    if (!g_prof_on) {
+        for (auto& r : g_prof_recs) {
+            g_event_pool.push_back(r.a);
+            g_event_pool.push_back(r.b);
+        }
+        g_prof_recs.clear();
+    }
+    return RS_OK;
+}
+
+int rs_profile_read(uint64_t* launches, double* total_ms, int max_kinds) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    for (int k = 0; k < max_kinds && k < KK_COUNT; ++k) {
+        if (launches) launches[k] = 0;
+        if (total_ms) total_ms[k] = 0.0;
+    }
+    for (auto& r : g_prof_recs) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (r.kind < max_kinds) {
+            if (launches) launches[r.kind] += 1;
+            if (total_ms) total_ms[r.kind] += ms;
+        }
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_prof_recs.clear();
+    return KK_COUNT;
+}
+
+const char* rs_kernel_kind_name(int kind) { return kernel_kind_name(kind); }
+
+rs_status rs_debug_set_spin_limit(uint32_t iterations) {
+    knobs().spin_limit = iterations ? iterations : kDefaultSpinLimit;
+    return RS_OK;
+}
+
+rs_status rs_debug_withhold_first_tile(int withhold) {
+    if (withhold)
+        knobs().debug |= DBG_WITHHOLD_FIRST_TILE;
+    else
+        knobs().debug &= ~DBG_WITHHOLD_FIRST_TILE;
+    return RS_OK;
+}
+
+}  // extern "C"

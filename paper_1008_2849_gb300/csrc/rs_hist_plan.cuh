@@ -1,0 +1,135 @@
+// rs_hist_plan.cuh -- the two small kernels that precede the scatter passes:
+//   k_hist4  one read of the keys builds all four digit histograms (the
+//            counting step of Sec. 3, for every digit at once);
+//   k_plan   exclusive prefix over the buckets of every digit (Sec. 3 "prefix
+//            sum"; Alg. 2 PrefixSum) and the pass plan.
+#pragma once
+
+#include "rs_device.cuh"
+
+namespace rs {
+
+// ---------------------------------------------------------------------------
+// k_hist4: H[p][b] for p = 0..3 in one pass over the keys, added into
+// hist[p * 256 + b] (which the caller zeroes).
+//
+// Keys are read as 16-byte vectors (a scalar head and tail handle a base that
+// is only 4-byte aligned).  Every warp aggregates equal digits with
+// match-any before touching the CTA's shared histogram, so that skewed keys
+// (all equal, AND of several words) do not serialise on one shared-memory
+// address.  The kernel also clears the look-back status array of the first
+// scatter pass.
+// ---------------------------------------------------------------------------
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
+        uint4* __restrict__ clear, uint32_t clear_vec4) {
+    __shared__ uint32_t s_h[PASSES * RADIX];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31;
+    for (uint32_t i = tid; i < PASSES * RADIX; i += THREADS) s_h[i] = 0;
+
+    const uint32_t gtid = blockIdx.x * THREADS + tid;
+    const uint32_t gsize = gridDim.x * THREADS;
+    for (uint32_t i = gtid; i < clear_vec4; i += gsize) clear[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+
+    uint32_t head = (uint32_t)(((16u - ((uintptr_t)keys & 15u)) & 15u) >> 2);
+    if (head > n) head = n;
+    const uint32_t body4 = (n - head) >> 2;
+    const uint32_t tail = head + body4 * 4;
+    const uint4* __restrict__ body = reinterpret_cast<const uint4*>(keys + head);
+
+    auto count_key = [&](uint32_t key, bool ok) {
+#pragma unroll
+        for (uint32_t p = 0; p < PASSES; ++p) {
+            const uint32_t d = (key >> (p * RADIX_BITS)) & (RADIX - 1);
+            const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0xffffffffu);
+            if (ok && lane == (uint32_t)(__ffs(peers) - 1))
+                atomicAdd(&s_h[p * RADIX + d], (uint32_t)__popc(peers));
+        }
+    };
+
+    // Warp-uniform loop: every iteration a warp takes 2 x 32 consecutive
+    // vectors, so all 32 lanes always take part in match-any.
+    const uint32_t gwarp = gtid >> 5;
+    const uint32_t nwarps = gsize >> 5;
+    for (uint32_t c = gwarp * 64; c < body4; c += nwarps * 64) {
+        const uint32_t i0 = c + lane, i1 = c + 32 + lane;
+        const bool ok0 = i0 < body4, ok1 = i1 < body4;
+        const uint4 v0 = ok0 ? ld_stream(body + i0) : make_uint4(0, 0, 0, 0);
+        const uint4 v1 = ok1 ? ld_stream(body + i1) : make_uint4(0, 0, 0, 0);
+        count_key(v0.x, ok0); count_key(v0.y, ok0); count_key(v0.z, ok0); count_key(v0.w, ok0);
+        count_key(v1.x, ok1); count_key(v1.y, ok1); count_key(v1.z, ok1); count_key(v1.w, ok1);
+    }
+    // At most 3 keys before the first 16-byte boundary and 3 after the last.
+    if (blockIdx.x == 0 && tid < 8) {
+        const uint32_t i = tid < 4 ? tid : tail + (tid - 4);
+        const bool ok = tid < 4 ? i < head : i < n;
+        if (ok) {
+            const uint32_t key = keys[i];
+#pragma unroll
+            for (uint32_t p = 0; p < PASSES; ++p)
+                atomicAdd(&s_h[p * RADIX + ((key >> (p * RADIX_BITS)) & (RADIX - 1))], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < PASSES * RADIX; i += THREADS) {
+        const uint32_t c = s_h[i];
+        if (c) atomicAdd(hist + i, c);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_plan: G[p][b] = sum_{b' < b} H[p][b'] and the pass plan.  One CTA of
+// 1024 threads, thread (p, b) = (tid / 256, tid % 256).
+//
+// A pass whose digit takes one value for every key is the identity (a stable
+// partition into one bucket).  Such passes are skipped, except that the
+// number of executed passes is kept even (one trivial pass is run if needed)
+// so that the ping-pong between the caller's arrays and the alternate
+// buffers ends in the caller's arrays.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_plan(Ctrl* __restrict__ ctrl, uint32_t n) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_trivial[PASSES];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t p = tid >> 8, b = tid & (RADIX - 1);
+    if (tid < PASSES) s_trivial[tid] = 0;
+    const uint32_t h = ctrl->hist[p][b];
+    uint32_t x = h;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t off = 0;
+    for (uint32_t w = p * (RADIX / 32); w < warp; ++w) off += s_warp[w];
+    ctrl->gofs[p][b] = off + x - h;
+    if (h == n) s_trivial[p] = 1;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t trivial[PASSES], executed = 0;
+        for (uint32_t q = 0; q < PASSES; ++q) {
+            trivial[q] = s_trivial[q];
+            executed += trivial[q] ? 0 : 1;
+        }
+        if (executed & 1) {
+            for (uint32_t q = 0; q < PASSES; ++q)
+                if (trivial[q]) { trivial[q] = 0; break; }
+        }
+        uint32_t parity = 0;
+        for (uint32_t q = 0; q < PASSES; ++q) {
+            if (trivial[q]) {
+                ctrl->dir[q] = DIR_SKIP;
+            } else {
+                ctrl->dir[q] = parity ? DIR_B_TO_A : DIR_A_TO_B;
+                parity ^= 1;
+            }
+        }
+    }
+}
+
+}  // namespace rs

@@ -1,0 +1,83 @@
+// rs_internal.h -- host-side interface between the C ABI (rs_api.cu) and the
+// kernel launchers (rs_sort.cu, rs_onesweep_*.cu).  Not installed, not part
+// of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rs.h"
+
+namespace rs {
+
+struct Ctrl;
+
+// Kernel kinds, for launch counting and per-kind event timing.
+enum KernelKind : int {
+    KK_HIST = 0,
+    KK_PLAN = 1,
+    KK_ONESWEEP = 2,
+    KK_COUNT
+};
+const char* kernel_kind_name(int kind);
+
+// Called around every kernel launch by the launchers.
+void note_launch_begin(int kind, cudaStream_t stream);
+void note_launch_end(int kind, cudaStream_t stream);
+
+// Tile shapes of the scatter kernel that this build instantiates.
+struct TileConfig {
+    int threads;
+    int items;
+};
+constexpr int NUM_TILE_CONFIGS = 3;
+extern const TileConfig kTileConfigs[NUM_TILE_CONFIGS];
+int smallest_tile();
+
+// Host-side knobs shared by every launch.
+struct Knobs {
+    int tile_config_pairs;   // index into kTileConfigs
+    int tile_config_keys;
+    uint32_t spin_limit;     // polls per look-back wait before ERR_TIMEOUT
+    uint32_t debug;          // DBG_* bits
+    int hist_ctas_per_sm;
+};
+Knobs& knobs();
+
+// Per-device facts cached on first use.
+struct DeviceInfo {
+    int sm_count;
+    uint32_t* sticky;        // device address of the sticky error word
+};
+rs_status device_info(DeviceInfo* out);
+
+// Workspace layout of an unsegmented sort of n items.
+struct Layout {
+    size_t ctrl, status0, status1, alt_keys, alt_vals, total;
+    uint32_t tiles;          // tiles of the smallest tile shape (status sizing)
+    bool wide_status;        // 64-bit status words (n >= 2^30)
+};
+Layout layout_for(size_t n, bool pairs);
+
+// Enqueue the whole sort of n items (1 <= n < 2^32) on `stream`, using the
+// caller's workspace (at least layout_for(n, pairs).total bytes).
+rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
+                       void* workspace, size_t workspace_bytes);
+
+// Enqueue the digit histograms of n keys into hist[4 * 256] (zeroed first).
+rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
+                             cudaStream_t stream);
+
+// Scatter-pass launchers, one per value flavour (separate translation units).
+rs_status launch_onesweep_keys(int cfg, bool wide, uint32_t* ka, uint32_t* kb, uint32_t n,
+                               uint32_t pass, Ctrl* ctrl, uint32_t* sticky, void* status,
+                               void* status_clear, cudaStream_t stream);
+rs_status launch_onesweep_pairs(int cfg, bool wide, uint32_t* ka, uint32_t* va, uint32_t* kb,
+                                uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
+                                uint32_t* sticky, void* status, void* status_clear,
+                                cudaStream_t stream);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace rs

@@ -1,0 +1,102 @@
+// rs_sort.cu -- histogram and plan kernels, workspace layout and the
+// enqueue sequence of one unsegmented sort.
+#include "rs_internal.h"
+#include "rs_hist_plan.cuh"
+
+namespace rs {
+
+const TileConfig kTileConfigs[NUM_TILE_CONFIGS] = {{256, 16}, {512, 16}, {512, 12}};
+
+int smallest_tile() {
+    int t = kTileConfigs[0].threads * kTileConfigs[0].items;
+    for (int i = 1; i < NUM_TILE_CONFIGS; ++i)
+        if (kTileConfigs[i].threads * kTileConfigs[i].items < t)
+            t = kTileConfigs[i].threads * kTileConfigs[i].items;
+    return t;
+}
+
+constexpr int HIST_THREADS = 512;
+
+Layout layout_for(size_t n, bool pairs) {
+    Layout L{};
+    const size_t tile = (size_t)smallest_tile();
+    L.tiles = (uint32_t)((n + tile - 1) / tile);
+    L.wide_status = n >= (size_t(1) << 30);
+    const size_t status_bytes = (size_t)L.tiles * RADIX * (L.wide_status ? 8 : 4);
+    size_t off = 0;
+    L.ctrl = off;
+    off = align_up(off + sizeof(Ctrl), 256);
+    L.status0 = off;
+    off = align_up(off + status_bytes, 256);
+    L.status1 = off;
+    off = align_up(off + status_bytes, 256);
+    L.alt_keys = off;
+    off = align_up(off + n * sizeof(uint32_t), 256);
+    L.alt_vals = off;
+    if (pairs) off = align_up(off + n * sizeof(uint32_t), 256);
+    L.total = off;
+    return L;
+}
+
+static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, void* clear,
+                             size_t clear_bytes, cudaStream_t stream) {
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
+    const uint32_t vec4 = (uint32_t)(n / 4);
+    uint32_t blocks = (uint32_t)(di.sm_count * knobs().hist_ctas_per_sm);
+    const uint32_t needed = (vec4 + 63) / 64 / (HIST_THREADS / 32) + 1;  // 64 vectors per warp
+    if (blocks > needed) blocks = needed;
+    if (blocks < 1) blocks = 1;
+    note_launch_begin(KK_HIST, stream);
+    k_hist4<HIST_THREADS><<<blocks, HIST_THREADS, 0, stream>>>(
+        keys, n, hist, static_cast<uint4*>(clear), (uint32_t)(clear_bytes / sizeof(uint4)));
+    note_launch_end(KK_HIST, stream);
+    return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
+                             cudaStream_t stream) {
+    if (cudaMemsetAsync(hist, 0, PASSES * RADIX * sizeof(uint32_t), stream) != cudaSuccess)
+        return RS_ERR_CUDA;
+    return launch_hist(keys, n, hist, nullptr, 0, stream);
+}
+
+rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
+                       void* workspace, size_t workspace_bytes) {
+    const bool pairs = vals != nullptr;
+    const Layout L = layout_for(n, pairs);
+    if (workspace == nullptr || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
+        return RS_ERR_INVALID_ARG;
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
+    char* ws = static_cast<char*>(workspace);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+    void* status[2] = {ws + L.status0, ws + L.status1};
+    const size_t status_bytes = L.status1 - L.status0;
+    uint32_t* alt_k = reinterpret_cast<uint32_t*>(ws + L.alt_keys);
+    uint32_t* alt_v = pairs ? reinterpret_cast<uint32_t*>(ws + L.alt_vals) : nullptr;
+
+    if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return RS_ERR_CUDA;
+    st = launch_hist(keys, n, &ctrl->hist[0][0], status[0], status_bytes, stream);
+    if (st != RS_OK) return st;
+    note_launch_begin(KK_PLAN, stream);
+    k_plan<<<1, 1024, 0, stream>>>(ctrl, n);
+    note_launch_end(KK_PLAN, stream);
+    if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
+
+    const int cfg = pairs ? knobs().tile_config_pairs : knobs().tile_config_keys;
+    for (uint32_t p = 0; p < PASSES; ++p) {
+        void* cur = status[p & 1];
+        void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;
+        st = pairs ? launch_onesweep_pairs(cfg, L.wide_status, keys, vals, alt_k, alt_v, n, p, ctrl,
+                                           di.sticky, cur, next, stream)
+                   : launch_onesweep_keys(cfg, L.wide_status, keys, alt_k, n, p, ctrl, di.sticky,
+                                          cur, next, stream);
+        if (st != RS_OK) return st;
+    }
+    return RS_OK;
+}
+
+}  // namespace rs

@@ -1,0 +1,209 @@
+"""Python binding of librs.so (argument marshalling only).
+
+Every function here forwards to the extern "C" entry point of the same name
+in ``include/rs.h``; the sort runs entirely in the library's CUDA kernels.
+PyTorch only supplies device memory and streams: tensors are passed as raw
+device pointers (``data_ptr()``) and the current stream's handle.  There is
+no fallback: if ``librs.so`` is missing or no sm_103a GPU is present, the
+calls raise.
+
+Tensors must be contiguous CUDA tensors of 4-byte elements (``torch.int32``
+or ``torch.uint32``); int32 tensors are read as their unsigned bit patterns.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librs.so")
+
+RS_OK = 0
+STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID_ARG", 2: "RS_ERR_OUT_OF_MEMORY", 3: "RS_ERR_CUDA",
+                4: "RS_ERR_TIMEOUT", 5: "RS_ERR_UNSUPPORTED", 6: "RS_ERR_BOUNDS",
+                7: "RS_ERR_BAD_SEGMENTS"}
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_u32 = ctypes.c_uint32
+_int = ctypes.c_int
+
+# name -> (restype, argtypes); mirrors include/rs.h
+SIGNATURES = {
+    "rs_sort_keys": (_int, [_vp, _sz]),
+    "rs_sort_pairs": (_int, [_vp, _vp, _sz]),
+    "rs_sort_keys_ex": (_int, [_vp, _sz, _vp, _vp, _sz]),
+    "rs_sort_pairs_ex": (_int, [_vp, _vp, _sz, _vp, _vp, _sz]),
+    "rs_workspace_bytes": (_sz, [_sz, _int, _u32]),
+    "rs_stream_status": (_int, [_vp]),
+    "rs_status_string": (ctypes.c_char_p, [_int]),
+    "rs_digit_histograms_ex": (_int, [_vp, _sz, _vp, _vp]),
+    "rs_sort_pairs_host": (_int, [_vp, _vp, _vp, _vp, _sz]),
+    "rs_launch_count": (ctypes.c_uint64, []),
+    "rs_profile_enable": (_int, [_int]),
+    "rs_profile_read": (_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), _int]),
+    "rs_kernel_kind_name": (ctypes.c_char_p, [_int]),
+    "rs_debug_set_spin_limit": (_int, [_u32]),
+    "rs_debug_withhold_first_tile": (_int, [_int]),
+}
+
+
+class RsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(code, code), status_string(code)))
+
+
+def lib():
+    """The loaded librs.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("librs.so not built: run `python -c \"import __graft_entry__ as g; "
+                                  "g.build()\"` or `python -m paper_1008_2849_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().rs_status_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != RS_OK:
+        raise RsError(code, where)
+
+
+def _dev_ptr(t, name: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.element_size() != 4 or t.dtype.is_floating_point:
+        raise TypeError("%s must hold 4-byte integers (int32/uint32), got %s" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def workspace_bytes(n: int, with_values: bool, num_segments: int = 0) -> int:
+    return int(lib().rs_workspace_bytes(int(n), 1 if with_values else 0, int(num_segments)))
+
+
+def alloc_workspace(n: int, with_values: bool, num_segments: int = 0, device=None):
+    """A torch uint8 CUDA tensor large enough for an _ex call (256-byte aligned)."""
+    import torch
+    nbytes = max(workspace_bytes(n, with_values, num_segments), 1)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+    pad = (-ws.data_ptr()) % 256
+    return ws[pad:pad + nbytes]
+
+
+def sort_keys(keys) -> None:
+    """Sort a CUDA tensor of keys in place (synchronous)."""
+    _check(lib().rs_sort_keys(_dev_ptr(keys, "keys"), keys.numel()), "rs_sort_keys")
+
+
+def sort_pairs(keys, vals) -> None:
+    """Sort (key, value) pairs in place by key, stable (synchronous)."""
+    if vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    _check(lib().rs_sort_pairs(_dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel()),
+           "rs_sort_pairs")
+
+
+def sort_keys_ex(keys, workspace, stream=None) -> None:
+    """Enqueue an in-place keys sort on ``stream`` (default: current stream)."""
+    _check(lib().rs_sort_keys_ex(_dev_ptr(keys, "keys"), keys.numel(), _stream_handle(stream),
+                                 workspace.data_ptr(), workspace.numel()), "rs_sort_keys_ex")
+
+
+def sort_pairs_ex(keys, vals, workspace, stream=None) -> None:
+    """Enqueue an in-place pairs sort on ``stream`` (default: current stream)."""
+    if vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    _check(lib().rs_sort_pairs_ex(_dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel(),
+                                  _stream_handle(stream), workspace.data_ptr(), workspace.numel()),
+           "rs_sort_pairs_ex")
+
+
+def stream_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device status code."""
+    return int(lib().rs_stream_status(_stream_handle(stream)))
+
+
+def check_stream(stream=None) -> None:
+    _check(stream_status(stream), "rs_stream_status")
+
+
+def digit_histograms(keys, out=None, stream=None):
+    """(4, 256) int32 CUDA tensor H[p, b] = #keys whose byte p is b."""
+    import torch
+    if out is None:
+        out = torch.empty((4, 256), dtype=torch.int32, device=keys.device)
+    _check(lib().rs_digit_histograms_ex(_dev_ptr(keys, "keys"), keys.numel(), _dev_ptr(out, "out"),
+                                        _stream_handle(stream)), "rs_digit_histograms_ex")
+    return out
+
+
+def sort_pairs_host(keys_in, vals_in, keys_out, vals_out) -> None:
+    """End-to-end sort of host arrays (numpy or CPU torch; pinned is fastest)."""
+    def hp(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or a.element_size() != 4 or not a.is_contiguous():
+                raise ValueError("host tensors must be contiguous CPU tensors of 4-byte ints")
+            return a.data_ptr()
+        if a.dtype.itemsize != 4 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous 4-byte ints")
+        return a.ctypes.data
+    n = keys_in.numel() if hasattr(keys_in, "numel") else keys_in.size
+    _check(lib().rs_sort_pairs_host(hp(keys_in), hp(vals_in), hp(keys_out), hp(vals_out), n),
+           "rs_sort_pairs_host")
+
+
+def launch_count() -> int:
+    return int(lib().rs_launch_count())
+
+
+def profile_enable(on: bool) -> None:
+    _check(lib().rs_profile_enable(1 if on else 0), "rs_profile_enable")
+
+
+def profile_read() -> dict:
+    """{kernel kind: (launches, total_ms)} since the last read; resets tallies."""
+    launches = (ctypes.c_uint64 * 16)()
+    ms = (ctypes.c_double * 16)()
+    k = lib().rs_profile_read(launches, ms, 16)
+    out = {}
+    for i in range(k):
+        name = lib().rs_kernel_kind_name(i).decode()
+        out[name] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+def debug_set_spin_limit(iterations: int) -> None:
+    _check(lib().rs_debug_set_spin_limit(int(iterations)), "rs_debug_set_spin_limit")
+
+
+def debug_withhold_first_tile(on: bool) -> None:
+    _check(lib().rs_debug_withhold_first_tile(1 if on else 0), "rs_debug_withhold_first_tile")

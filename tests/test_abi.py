@@ -1,0 +1,85 @@
+"""CPU-only checks of the C ABI: the library builds, loads without a GPU,
+exports every entry point include/rs.h declares, and rejects bad arguments
+on the host before touching CUDA."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(rs_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1008_2849_gb300 import build, rs
+    build.build_library()
+    return rs.lib()
+
+
+def test_header_declares_core_calls():
+    names = header_functions()
+    for must in ("rs_sort_keys", "rs_sort_pairs", "rs_sort_keys_ex", "rs_sort_pairs_ex",
+                 "rs_workspace_bytes", "rs_stream_status", "rs_status_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), "librs.so does not export %s" % name
+
+
+def test_binding_covers_header():
+    from paper_1008_2849_gb300 import rs
+    assert sorted(rs.SIGNATURES) == header_functions()
+
+
+def test_status_strings(lib):
+    from paper_1008_2849_gb300 import rs
+    for code in range(0, 8):
+        s = rs.status_string(code)
+        assert s and s != "unknown status"
+    assert rs.status_string(99) == "unknown status"
+
+
+def test_workspace_bytes(lib):
+    from paper_1008_2849_gb300 import rs
+    assert rs.workspace_bytes(0, True) == 0
+    small = rs.workspace_bytes(1000, False)
+    pairs = rs.workspace_bytes(1000, True)
+    assert pairs > small > 0
+    n = 1 << 28
+    ws = rs.workspace_bytes(n, True)
+    # alternate key and value buffers plus look-back status and control
+    # at most two status arrays of 1 KiB per 4096-item tile, plus 64 KiB
+    assert 8 * n <= ws <= 8 * n + 2 * (n // 4096) * 1024 + 65536
+    assert ws % 256 == 0
+
+
+def test_host_side_argument_errors(lib):
+    from paper_1008_2849_gb300 import rs
+    # All of these are rejected before any CUDA call.
+    assert lib.rs_sort_keys(None, 5) == 1                  # null keys
+    assert lib.rs_sort_pairs(ctypes.c_void_p(4096), None, 5) == 1   # null values
+    assert lib.rs_sort_keys(ctypes.c_void_p(4096), 1 << 32) == 5    # n >= 2^32
+    assert lib.rs_sort_keys(ctypes.c_void_p(4098), 5) == 1          # misaligned
+    # keys and values overlap
+    assert lib.rs_sort_pairs(ctypes.c_void_p(4096), ctypes.c_void_p(4096 + 8), 5) == 1
+    # n = 0 is a no-op
+    assert lib.rs_sort_keys(None, 0) == 0
+    assert lib.rs_sort_pairs_ex(ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), 100, None, None, 0) == 1
+    assert lib.rs_digit_histograms_ex(ctypes.c_void_p(4096), 10, None, None) == 1
+    assert lib.rs_sort_pairs_host(None, None, None, None, 10) == 1
