@@ -233,7 +233,7 @@ def main():
     traffic = recorded_traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "kernel": "k_onesweep<512,16,pairs>", "peak_source": peak_src + " (hbm_gbs, copy)",
+            "kernel": "k_onesweep (pairs, default tile shape)", "peak_source": peak_src + " (hbm_gbs, copy)",
             "avg_launch_ms": os_ms / os_launches if os_launches else None,
             "algorithmic_bytes_per_launch": algo_bytes,
             "hist_avg_launch_ms": hist_ms / hist_launches if hist_launches else None,

@@ -127,6 +127,30 @@ int rs_profile_read(uint64_t* launches, double* total_ms, int max_kinds);
 /* Name of kernel kind k, or NULL past the last kind. */
 const char* rs_kernel_kind_name(int kind);
 
+/* ---- tuning (used by the autotuner and the benchmarks) ------------------
+ * Process-wide host settings read at every launch; change them only while no
+ * other thread is enqueueing a sort.  Results never depend on them, only
+ * speed does. */
+typedef enum rs_tune_knob {
+    RS_TUNE_TILE_PAIRS = 0,       /* tile shape index (rs_tile_shape) of key-value passes */
+    RS_TUNE_TILE_KEYS = 1,        /* tile shape index of keys-only passes */
+    RS_TUNE_HIST_CTAS_PER_SM = 2, /* CTAs per SM of the histogram kernel, 1..16 */
+    RS_TUNE_HIST_MODE = 3         /* 0: lane atomics, 1: lane-0 group + atomics, 2: ballot groups */
+} rs_tune_knob;
+
+/* Set a knob; RS_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
+rs_status rs_tune_set(int knob, int value);
+
+/* Current value of a knob, or -1 for an unknown knob. */
+int rs_tune_get(int knob);
+
+/* Number of tile shapes of the scatter pass compiled into this build. */
+int rs_tile_shape_count(void);
+
+/* Shape `index`: CUDA threads per CTA and items per thread (a tile holds
+ * threads * items_per_thread items).  RS_ERR_INVALID_ARG past the end. */
+rs_status rs_tile_shape(int index, int* threads, int* items_per_thread);
+
 /* ---- fault-injection knobs for tests (host-side settings) ------------- */
 
 /* Iteration limit of every look-back wait (0 restores the default). */

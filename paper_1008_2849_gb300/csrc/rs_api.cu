@@ -152,7 +152,7 @@ rs_status plain_sort(uint32_t* keys, uint32_t* vals, size_t n) {
 }  // namespace
 
 Knobs& knobs() {
-    static Knobs k{1, 1, kDefaultSpinLimit, 0, 4};
+    static Knobs k{3, 3, kDefaultSpinLimit, 0, 4, 0};
     return k;
 }
 
@@ -350,6 +350,46 @@ int rs_profile_read(uint64_t* launches, double* total_ms, int max_kinds) {
 }
 
 const char* rs_kernel_kind_name(int kind) { return kernel_kind_name(kind); }
+
+rs_status rs_tune_set(int knob, int value) {
+    Knobs& k = knobs();
+    switch (knob) {
+    case 0:
+    case 1:
+        if (value < 0 || value >= NUM_TILE_CONFIGS) return RS_ERR_INVALID_ARG;
+        (knob == 0 ? k.tile_config_pairs : k.tile_config_keys) = value;
+        return RS_OK;
+    case 2:
+        if (value < 1 || value > 16) return RS_ERR_INVALID_ARG;
+        k.hist_ctas_per_sm = value;
+        return RS_OK;
+    case 3:
+        if (value < 0 || value > 2) return RS_ERR_INVALID_ARG;
+        k.hist_mode = value;
+        return RS_OK;
+    default: return RS_ERR_INVALID_ARG;
+    }
+}
+
+int rs_tune_get(int knob) {
+    const Knobs& k = knobs();
+    switch (knob) {
+    case 0: return k.tile_config_pairs;
+    case 1: return k.tile_config_keys;
+    case 2: return k.hist_ctas_per_sm;
+    case 3: return k.hist_mode;
+    default: return -1;
+    }
+}
+
+int rs_tile_shape_count(void) { return NUM_TILE_CONFIGS; }
+
+rs_status rs_tile_shape(int index, int* threads, int* items_per_thread) {
+    if (index < 0 || index >= NUM_TILE_CONFIGS) return RS_ERR_INVALID_ARG;
+    if (threads) *threads = kTileConfigs[index].threads;
+    if (items_per_thread) *items_per_thread = kTileConfigs[index].items;
+    return RS_OK;
+}
 
 rs_status rs_debug_set_spin_limit(uint32_t iterations) {
     knobs().spin_limit = iterations ? iterations : kDefaultSpinLimit;

@@ -79,9 +79,82 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
 
+// Asynchronous 4-byte global -> shared copy (no register staging); completes
+// at cp_async_wait_all().
+__device__ __forceinline__ void cp_async4(uint32_t* smem_dst, const uint32_t* gmem_src) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// ---- mbarrier and TMA bulk copies (sm_90+ async proxy) --------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Make barrier initialisation visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Order this thread's earlier ordinary shared-memory accesses before later
+// async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes) : "memory");
+}
+// Arrive on `bar` once all of this thread's earlier cp.async copies are done.
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// One bulk copy global -> shared, completing `bytes` of the barrier's
+// transaction count.  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* smem_dst, const void* gmem_src, uint32_t bytes,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(smem_dst)), "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void record_error(Ctrl* ctrl, uint32_t* sticky, uint32_t bits) {
     atomicOr(&ctrl->err, bits);
     atomicOr(sticky, bits);
+}
+
+// Lanes of the warp whose BITS-bit label equals this lane's label, built from
+// one ballot per label bit: a lane keeps the lanes that agree with it on
+// every bit.  (The native match instruction is far slower on this part.)
+template <int BITS>
+__device__ __forceinline__ uint32_t match_label(uint32_t label) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const uint32_t bit = (label >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= m ^ (bit - 1u);  // bit = 1: m; bit = 0: ~m
+    }
+    return peers;
+}
+
+// Lanes l of the warp for which base + l < limit (a prefix of the warp).
+__device__ __forceinline__ uint32_t prefix_lanes(uint32_t base, uint32_t limit) {
+    if (limit <= base) return 0u;
+    const uint32_t k = limit - base;
+    return k >= 32u ? 0xffffffffu : ((1u << k) - 1u);
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

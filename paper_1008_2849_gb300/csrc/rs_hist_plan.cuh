@@ -14,13 +14,23 @@ namespace rs {
 // hist[p * 256 + b] (which the caller zeroes).
 //
 // Keys are read as 16-byte vectors (a scalar head and tail handle a base that
-// is only 4-byte aligned).  Every warp aggregates equal digits with
-// match-any before touching the CTA's shared histogram, so that skewed keys
-// (all equal, AND of several words) do not serialise on one shared-memory
-// address.  The kernel also clears the look-back status array of the first
-// scatter pass.
+// is only 4-byte aligned) into a CTA-private shared histogram, which is added
+// to the global one at the end.  How a warp updates the shared histogram is
+// a tuning choice (MODE):
+//   HIST_ATOMIC   every lane adds 1 to its bin;
+//   HIST_LEADER   lanes whose digit equals lane 0's are added as one group
+//                 (cheap, and it removes the worst shared-memory serialisation
+//                 when most keys share a digit), the others add 1 each;
+//   HIST_MATCH    lanes are grouped by digit with one ballot per digit bit and
+//                 the lowest lane of every group adds the group's size.
+// The kernel also clears the look-back status array of the first scatter
+// pass.
 // ---------------------------------------------------------------------------
-template <int THREADS>
+constexpr int HIST_ATOMIC = 0;
+constexpr int HIST_LEADER = 1;
+constexpr int HIST_MATCH = 2;
+
+template <int THREADS, int MODE>
 __global__ void __launch_bounds__(THREADS)
 k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
         uint4* __restrict__ clear, uint32_t clear_vec4) {
@@ -44,14 +54,25 @@ k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hi
 #pragma unroll
         for (uint32_t p = 0; p < PASSES; ++p) {
             const uint32_t d = (key >> (p * RADIX_BITS)) & (RADIX - 1);
-            const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0xffffffffu);
-            if (ok && lane == (uint32_t)(__ffs(peers) - 1))
-                atomicAdd(&s_h[p * RADIX + d], (uint32_t)__popc(peers));
+            uint32_t* bin = &s_h[p * RADIX + d];
+            if (MODE == HIST_ATOMIC) {
+                if (ok) atomicAdd(bin, 1u);
+            } else if (MODE == HIST_LEADER) {
+                const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+                const uint32_t same = __ballot_sync(0xffffffffu, ok && d == d0);
+                if (ok) {
+                    if (d != d0) atomicAdd(bin, 1u);
+                    else if (lane == (uint32_t)(__ffs(same) - 1)) atomicAdd(bin, (uint32_t)__popc(same));
+                }
+            } else {
+                const uint32_t peers = match_label<RADIX_BITS>(d) & __ballot_sync(0xffffffffu, ok);
+                if (ok && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(bin, (uint32_t)__popc(peers));
+            }
         }
     };
 
     // Warp-uniform loop: every iteration a warp takes 2 x 32 consecutive
-    // vectors, so all 32 lanes always take part in match-any.
+    // vectors, so all 32 lanes always take part in the warp votes.
     const uint32_t gwarp = gtid >> 5;
     const uint32_t nwarps = gsize >> 5;
     for (uint32_t c = gwarp * 64; c < body4; c += nwarps * 64) {

@@ -30,8 +30,9 @@ void note_launch_end(int kind, cudaStream_t stream);
 struct TileConfig {
     int threads;
     int items;
+    int min_blocks;  // CTAs per SM the register budget is sized for
 };
-constexpr int NUM_TILE_CONFIGS = 3;
+constexpr int NUM_TILE_CONFIGS = 6;
 extern const TileConfig kTileConfigs[NUM_TILE_CONFIGS];
 int smallest_tile();
 
@@ -42,6 +43,7 @@ struct Knobs {
     uint32_t spin_limit;     // polls per look-back wait before ERR_TIMEOUT
     uint32_t debug;          // DBG_* bits
     int hist_ctas_per_sm;
+    int hist_mode;           // HIST_ATOMIC / HIST_LEADER / HIST_MATCH
 };
 Knobs& knobs();
 

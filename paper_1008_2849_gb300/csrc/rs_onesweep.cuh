@@ -1,8 +1,9 @@
 // rs_onesweep.cuh -- k_onesweep, one stable counting-sort pass (Sec. 3/4)
-// per launch: per-tile ranking with warp match-any, a decoupled look-back
-// across tiles for the tile's share of every bucket, staging of the tile in
-// shared memory in bucket order, and coalesced stores of every bucket run --
-// the GPU counterpart of the software write-combining buffers of Sec. 2.
+// per launch, as a persistent kernel: per-tile ranking, a decoupled
+// look-back across tiles for the tile's share of every bucket, staging of the
+// tile in shared memory in bucket order, and coalesced stores of every bucket
+// run -- the GPU counterpart of the software write-combining buffers of
+// Sec. 2.
 #pragma once
 
 #include "rs_device.cuh"
@@ -10,214 +11,403 @@
 namespace rs {
 
 // ---------------------------------------------------------------------------
-// k_onesweep: one stable counting-sort pass by digit `pass` over tiles of
-// TILE = THREADS * ITEMS items.
-//
-// Layout of a tile in registers: warp w holds tile items [w*32*ITEMS,
-// (w+1)*32*ITEMS); item j of lane l is tile item w*32*ITEMS + j*32 + l, so
-// every load instruction of a warp reads 128 contiguous bytes, and the
-// (warp, j, lane) order is the input order -- which is what keeps the
-// ranking stable.
-//
-// Ranking: for every item, match-any gives the lanes of the warp holding the
-// same digit; the lowest of them adds the group's size to the warp's
-// counter of that digit; an item's rank is the counter's old value plus the
-// number of its peers on lower lanes.  Warp counters are then turned into
-// per-warp exclusive offsets and the tile's per-digit count c[b].
-//
-// Look-back: the tile publishes c[b] (flag AGG; the first tile publishes
-// INC), then thread b walks back over the tiles before it, adding AGG counts
-// until it meets an INC prefix, and publishes its own inclusive prefix
-// (INC).  Tile ids come from an atomic counter, so every tile before this
-// one belongs to a CTA that is already running and will publish.  Every wait
-// is bounded by spin_limit polls; when it runs out the kernel records
-// ERR_TIMEOUT and the CTA (and every CTA that sees the error) writes nothing.
-//
-// Scatter: keys are written to shared memory at their tile position (bucket
-// order), then read back in slot order and stored to
-//   dst[G[b] + prefix_before_this_tile[b] + (slot - tile_excl[b])],
-// so consecutive threads store consecutive addresses of one bucket run.
-// Values follow through the same staging buffer.  Every global store is
-// checked against n (ERR_BOUNDS instead of a fault).
+// Shared-memory plan of k_onesweep (all in 32-bit words):
+//   in_k[2][TILE]        input keys of the current and the next tile; the
+//                        current tile's values are staged here once its keys
+//                        are ranked
+//   in_v[TILE]           input values of the current tile (key-value sorts)
+//   stage[TILE]          the current tile's keys in bucket order
+//   wcnt[WARPS][RADIX]   per-warp digit counts of a tile, turned into per-warp
+//                        tile positions while the tile is ranked
+//   mask[WARPS][RADIX]   per-warp peer masks of the ranking (zero between uses)
 // ---------------------------------------------------------------------------
-template <int THREADS, int ITEMS, bool PAIRS, typename S>
-__global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 2 : 4))
+template <int THREADS, int ITEMS, bool PAIRS>
+struct OnesweepSmem {
+    static constexpr uint32_t WARPS = THREADS / 32;
+    static constexpr uint32_t TILE = THREADS * ITEMS;
+    static constexpr uint32_t IN_K = 0;
+    static constexpr uint32_t IN_V = IN_K + 2 * TILE;
+    static constexpr uint32_t STG = IN_V + (PAIRS ? TILE : 0);
+    static constexpr uint32_t WCNT = STG + TILE;
+    static constexpr uint32_t MASK = WCNT + WARPS * RADIX;
+    static constexpr uint32_t WORDS = MASK + WARPS * RADIX;
+    static constexpr size_t BYTES = WORDS * sizeof(uint32_t);
+};
+
+// ---------------------------------------------------------------------------
+// k_onesweep: one stable counting-sort pass by digit `pass` over tiles of
+// TILE = THREADS * ITEMS items, run by a persistent grid.
+//
+// Tile flow inside a CTA (tile ids come from an atomic counter, in increasing
+// order per CTA): while tile i is ranked, the keys of tile i+1 are already
+// being copied into the other key buffer by the tensor memory accelerator
+// (one bulk copy, completing on an mbarrier); tile i+1's values follow as soon
+// as tile i's values have been staged.  A base that is not 16-byte aligned, or
+// a ragged last tile, falls back to per-thread 4-byte asynchronous copies on
+// the same barrier.  As soon as tile i+1's keys have landed its per-warp digit
+// counts are taken and its tile counts published.
+//
+// Item order: warp w owns tile items [w*32*ITEMS, (w+1)*32*ITEMS); its item j
+// on lane l is tile item w*32*ITEMS + j*32 + l, so the (warp, j, lane) order
+// is the input order -- which is what keeps the ranking stable.
+//
+// Per tile:
+//  1. From the per-warp counts: the tile's count c[b] of every digit, its
+//     exclusive prefix over digits, and every warp's first tile position for
+//     every digit (warps before it come first).
+//  2. Ranking (per warp, item slot j at a time): the lanes holding the same
+//     digit come from one ballot per digit bit (odd slots) or from a shared
+//     peer mask each lane ORs its bit into (even slots) -- alternating keeps
+//     both the integer and the shared-memory pipes busy; the lowest lane of the
+//     group adds the group's size to the warp's position counter of the digit;
+//     an item's tile position is the counter's old value plus the number of its
+//     peers on lower lanes.  The key is written straight to that position of
+//     the staging buffer.
+//  3. Look-back (threads b < 256): read the status words of the WINDOW tiles
+//     before this one at once, add AGG counts from the nearest one on until an
+//     INC prefix, re-reading from the first tile that has not published yet;
+//     publish this tile's inclusive prefix (INC).  Meanwhile the other warps
+//     count the next tile, whose counts are published right after.  A CTA takes
+//     its next tile id only after its look-back, so between taking an id and
+//     publishing that tile's counts it waits on no other CTA; every tile before
+//     this one has therefore published its counts or will without waiting, and
+//     the earliest unfinished tile always progresses.  Every wait is bounded by
+//     spin_limit polls; when it runs out the kernel records ERR_TIMEOUT and
+//     CTAs that see the error write nothing more.
+//  4. Values are staged at the same positions (in the key buffer, free now).
+//  5. Slot s of the staging buffer is stored to
+//       dst[G[b] + prefix_before_this_tile[b] + (s - tile_excl[b])],
+//     so consecutive threads store consecutive addresses of one bucket run.
+//     Every global store is checked against n (ERR_BOUNDS instead of a fault).
+// ---------------------------------------------------------------------------
+template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WINDOW>
+__global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
            uint32_t* __restrict__ kb, uint32_t* __restrict__ vb,
-           uint32_t n, uint32_t pass, Ctrl* __restrict__ ctrl, uint32_t* __restrict__ sticky,
-           S* __restrict__ status, S* __restrict__ status_clear,
-           uint32_t spin_limit, uint32_t debug) {
-    static_assert(THREADS >= (int)RADIX && THREADS % 32 == 0, "one thread per digit");
+           uint32_t n, uint32_t pass, uint32_t num_tiles, Ctrl* __restrict__ ctrl,
+           uint32_t* __restrict__ sticky, S* __restrict__ status, S* __restrict__ status_clear,
+           uint32_t clear_words, uint32_t spin_limit, uint32_t debug) {
+    using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
     using SW = StatusWord<S>;
-    constexpr uint32_t WARPS = THREADS / 32;
-    constexpr uint32_t TILE = THREADS * ITEMS;
+    static_assert(THREADS >= (int)RADIX && THREADS % 32 == 0, "one thread per digit");
+    constexpr uint32_t WARPS = L::WARPS;
+    constexpr uint32_t TILE = L::TILE;
     constexpr uint32_t WARP_ITEMS = 32 * ITEMS;
+    constexpr int WIN = sizeof(S) == 8 ? WINDOW / 2 : WINDOW;  // same registers either way
+    constexpr uint32_t LB_WARPS = RADIX / 32;                   // warps of the look-back
+    constexpr bool SPARE = WARPS > LB_WARPS;                    // warps free to count meanwhile
+    constexpr uint32_t ISSUER = THREADS - 1;                    // issues the bulk copies
+    static_assert(L::BYTES + 4096 <= 232448, "shared memory plan exceeds one CTA's limit");
 
-    __shared__ uint32_t s_wcnt[WARPS][RADIX + 1];  // bin RADIX: items past n
-    __shared__ uint32_t s_excl[RADIX];
-    __shared__ uint32_t s_gofs[RADIX];
+    extern __shared__ uint4 s_dyn[];
+    uint32_t* const smem = reinterpret_cast<uint32_t*>(s_dyn);
+    uint32_t* const s_stage = smem + L::STG;
+    uint32_t* const s_wcnt = smem + L::WCNT;
+    const uint32_t* const s_in_v = smem + L::IN_V;
+    __shared__ uint32_t s_gbase[RADIX];  // G[pass][b]
+    __shared__ uint32_t s_gofs[RADIX];   // G + before_tile - tile_excl, per tile
     __shared__ uint32_t s_scan[RADIX / 32];
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_abort;
-    extern __shared__ uint32_t s_stage[];  // TILE words
+    __shared__ uint32_t s_ids[4];
+    __shared__ uint32_t s_flag;
+    __shared__ uint32_t s_err_seen;  // the call's error word, read once per tile
+    __shared__ __align__(8) uint64_t s_bar[3];  // key buffers 0 and 1, values
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // Clear this CTA's slot of the next pass's status array (its last user,
-    // the previous pass, has completed).
-    if (status_clear != nullptr)
-        for (uint32_t b = tid; b < RADIX; b += THREADS)
-            status_clear[(size_t)blockIdx.x * RADIX + b] = 0;
-
     const uint32_t dir = ctrl->dir[pass];
-    if (dir == DIR_SKIP) return;
+    if (dir == DIR_SKIP) {
+        // No tiles in this pass: clear the whole next status array here.
+        if (status_clear != nullptr)
+            for (uint32_t i = blockIdx.x * THREADS + tid; i < clear_words; i += gridDim.x * THREADS)
+                status_clear[i] = 0;
+        return;
+    }
     const uint32_t* __restrict__ src_k = dir == DIR_A_TO_B ? ka : kb;
     uint32_t* __restrict__ dst_k = dir == DIR_A_TO_B ? kb : ka;
     const uint32_t* __restrict__ src_v = dir == DIR_A_TO_B ? va : vb;
     uint32_t* __restrict__ dst_v = dir == DIR_A_TO_B ? vb : va;
 
-    for (uint32_t i = tid; i < WARPS * (RADIX + 1); i += THREADS) (&s_wcnt[0][0])[i] = 0;
+    for (uint32_t i = tid; i < 2 * WARPS * RADIX / 4; i += THREADS)
+        reinterpret_cast<uint4*>(s_wcnt)[i] = make_uint4(0, 0, 0, 0);  // wcnt and mask
+    if (tid < RADIX) s_gbase[tid] = ctrl->gofs[pass][tid];
     if (tid == 0) {
-        s_tile = atomicAdd(&ctrl->tile_ctr[pass], 1u);
-        s_abort = 0;
+        for (int b = 0; b < 3; ++b) mbar_init(&s_bar[b], 1);
+        fence_mbar_init();
+        s_ids[0] = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+        s_flag = 0;
+        s_err_seen = 0;
     }
     __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint32_t tile_base = tile * TILE;
-    const uint32_t valid = (n - tile_base) < TILE ? (n - tile_base) : TILE;
+
+    auto tile_valid = [&](uint32_t t) { return (n - t * TILE) < TILE ? (n - t * TILE) : TILE; };
+
+    // Start copying the `valid` items at src + t*TILE into dst (collective):
+    // one bulk copy of the 16-byte-aligned prefix, per-thread copies for the
+    // rest, all completing on `bar`.
+    auto issue_copy = [&](uint32_t* dst, const uint32_t* src, uint32_t t, uint64_t* bar) {
+        const uint32_t valid = tile_valid(t);
+        const uint32_t* from = src + (size_t)t * TILE;
+        const uint32_t nb = ((uintptr_t)from & 15u) == 0 ? (valid & ~3u) : 0u;
+        if (nb < valid) {  // CTA-uniform
+            bool issued = false;
+            for (uint32_t i = nb + tid; i < valid; i += THREADS) {
+                cp_async4(dst + i, from + i);
+                issued = true;
+            }
+            if (issued) cp_async_mbar_arrive(bar);
+            __syncthreads();  // every pending count is raised before the arrival below
+        }
+        if (tid == ISSUER) {
+            // The buffer was last written by ordinary stores: order those
+            // before the bulk copy's writes.
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, nb * 4u);
+            if (nb) tma_load_1d(dst, from, nb * 4u, bar);
+        }
+    };
+
+    uint32_t phase = 0;  // bit b: parity of the next completion of s_bar[b]
+    auto wait_bar = [&](uint32_t b) {
+        uint32_t polls = 0;
+        while (!mbar_try_wait(&s_bar[b], (phase >> b) & 1u)) {
+            if (++polls > spin_limit) {
+                record_error(ctrl, sticky, ERR_TIMEOUT);
+                s_flag = 1;
+                break;
+            }
+        }
+        phase ^= 1u << b;
+    };
     const uint32_t shift = pass * RADIX_BITS;
     const uint32_t wofs = warp * WARP_ITEMS;
-
-    uint32_t key[ITEMS];
-    uint32_t val[ITEMS];
+    // Count the slots of warp w of the tile in key buffer b into wcnt row w.
+    auto count_slots_of = [&](uint32_t b, uint32_t valid, uint32_t w) {
+        const uint32_t* keys = smem + L::IN_K + b * TILE;
+        uint32_t* row = s_wcnt + w * RADIX;
+        const uint32_t base = w * WARP_ITEMS;
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t li = wofs + j * 32 + lane;
-        key[j] = li < valid ? ld_stream(src_k + tile_base + li) : 0u;
-        if (PAIRS) val[j] = li < valid ? ld_stream(src_v + tile_base + li) : 0u;
-    }
-
-    uint32_t rank[ITEMS];
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t li = base + j * 32 + lane;
+            if (li < valid) atomicAdd(&row[(keys[li] >> shift) & (RADIX - 1)], 1u);
+        }
+    };
+    // Publish the counts of tile t (per-warp counts in wcnt): AGG, or INC for
+    // tile 0.
+    auto publish_counts = [&](uint32_t t) {
+        if (tid < RADIX) {
+            uint32_t c = 0;
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t li = wofs + j * 32 + lane;
-        const uint32_t d = li < valid ? (key[j] >> shift) & (RADIX - 1) : RADIX;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t leader = __ffs(peers) - 1;
-        uint32_t before = 0;
-        if (lane == leader) before = atomicAdd(&s_wcnt[warp][d], (uint32_t)__popc(peers));
-        before = __shfl_sync(0xffffffffu, before, leader);
-        rank[j] = before + __popc(peers & lanemask_lt());
-    }
+            for (uint32_t w = 0; w < WARPS; ++w) c += s_wcnt[w * RADIX + tid];
+            const bool withhold = (debug & DBG_WITHHOLD_FIRST_TILE) && t == 0;
+            if (!withhold)
+                st_relaxed(status + (size_t)t * RADIX + tid, (t == 0 ? SW::INC : SW::AGG) | (S)c);
+        }
+    };
+
+    // Prologue: the first tile's data and counts; the second tile's id is taken
+    // once they are published.
+    if (s_ids[0] >= num_tiles) return;
+    issue_copy(smem + L::IN_K, src_k, s_ids[0], &s_bar[0]);
+    if (PAIRS) issue_copy(smem + L::IN_V, src_v, s_ids[0], &s_bar[2]);
+    wait_bar(0);
+    count_slots_of(0, tile_valid(s_ids[0]), warp);
+    __syncthreads();
+    publish_counts(s_ids[0]);
+    if (tid == 0) s_ids[1] = atomicAdd(&ctrl->tile_ctr[pass], 1u);
     __syncthreads();
 
-    // Per digit: exclusive offsets of the warps and the tile's count; publish
-    // the count; exclusive prefix over digits inside the tile.
-    uint32_t count = 0;
-    if (tid < RADIX) {
-#pragma unroll
-        for (uint32_t w = 0; w < WARPS; ++w) {
-            const uint32_t c = s_wcnt[w][tid];
-            s_wcnt[w][tid] = count;
-            count += c;
-        }
-        const bool withhold = (debug & DBG_WITHHOLD_FIRST_TILE) && tile == 0;
-        if (!withhold)
-            st_relaxed(status + (size_t)tile * RADIX + tid, (tile == 0 ? SW::INC : SW::AGG) | (S)count);
-    }
-    uint32_t x = count;
-#pragma unroll
-    for (uint32_t o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (tid < RADIX && lane == 31) s_scan[warp] = x;
-    __syncthreads();
+    const uint32_t lt = lanemask_lt();
 
-    if (tid < RADIX) {
-        uint32_t off = 0;
-        for (uint32_t w = 0; w < warp; ++w) off += s_scan[w];
-        const uint32_t excl_in_tile = off + x - count;
-        s_excl[tid] = excl_in_tile;
+    for (uint32_t it = 0;; ++it) {
+        const uint32_t tile = s_ids[it & 3];
+        if (tile >= num_tiles) break;
+        const uint32_t buf = it & 1;
+        const uint32_t nxt = s_ids[(it + 1) & 3];
+        const bool have_next = nxt < num_tiles;
+        if (have_next) issue_copy(smem + L::IN_K + (buf ^ 1) * TILE, src_k, nxt, &s_bar[buf ^ 1]);
+        if (tid == ISSUER) s_err_seen = ld_relaxed(&ctrl->err);
+        if (status_clear != nullptr)
+            for (uint32_t b = tid; b < RADIX; b += THREADS)
+                status_clear[(size_t)tile * RADIX + b] = 0;
 
-        S before_tile = 0;  // items of digit tid in all earlier tiles
-        if (tile > 0) {
-            uint32_t t = tile - 1;
-            uint32_t spins = 0;
-            bool stop = false;
-            while (!stop) {
-                const S s = ld_relaxed(status + (size_t)t * RADIX + tid);
-                const S flag = s & SW::FLAGS;
-                if (flag != 0) {
-                    before_tile += s & SW::VALUE;
-                    if (flag == SW::INC || t == 0) break;
-                    --t;
-                    continue;
-                }
-                if (++spins > spin_limit) {
-                    record_error(ctrl, sticky, ERR_TIMEOUT);
-                    __threadfence();  // error visible before the INC below
-                    s_abort = 1;
-                    stop = true;
-                } else if ((spins & 63u) == 0 && ld_relaxed(&ctrl->err) != 0) {
-                    s_abort = 1;
-                    stop = true;
-                }
-            }
-            st_relaxed(status + (size_t)tile * RADIX + tid,
-                       SW::INC | ((before_tile + (S)count) & SW::VALUE));
-        }
-        s_gofs[tid] = ctrl->gofs[pass][tid] + (uint32_t)before_tile - excl_in_tile;
-    }
-    if (tid == 0) {
-        __threadfence();
-        if (ld_relaxed(&ctrl->err) != 0) s_abort = 1;
-    }
-    __syncthreads();
-    if (s_abort) return;
+        const uint32_t valid = tile_valid(tile);
+        uint32_t* const in_k = smem + L::IN_K + buf * TILE;
 
-    // Stage the tile in bucket order.
+        // ---- 1. counts, prefix over digits, per-warp positions -----------
+        uint32_t count = 0;
+        if (tid < RADIX) {
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t li = wofs + j * 32 + lane;
-        if (li < valid) {
-            const uint32_t d = (key[j] >> shift) & (RADIX - 1);
-            const uint32_t pos = s_excl[d] + s_wcnt[warp][d] + rank[j];
-            s_stage[pos] = key[j];
-            rank[j] = pos;
+            for (uint32_t w = 0; w < WARPS; ++w) count += s_wcnt[w * RADIX + tid];
         }
-    }
-    __syncthreads();
-
-    bool bad = false;
-    uint32_t gpos[ITEMS];
+        uint32_t x = count;
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-        const uint32_t s = k * THREADS + tid;
-        gpos[k] = 0xffffffffu;
-        if (s < valid) {
-            const uint32_t kk = s_stage[s];
-            const uint32_t g = s_gofs[(kk >> shift) & (RADIX - 1)] + s;
-            gpos[k] = g;
-            if (g < n) dst_k[g] = kk;
-            else bad = true;
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-    }
-    if (PAIRS) {
+        if (tid < RADIX && lane == 31) s_scan[warp] = x;
         __syncthreads();
+        uint32_t excl_in_tile = 0;
+        if (tid < RADIX) {
+            uint32_t off = 0;
+            for (uint32_t w = 0; w < warp; ++w) off += s_scan[w];
+            excl_in_tile = off + x - count;
+            uint32_t run = excl_in_tile;
+#pragma unroll
+            for (uint32_t w = 0; w < WARPS; ++w) {
+                const uint32_t c = s_wcnt[w * RADIX + tid];
+                s_wcnt[w * RADIX + tid] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+
+        // ---- 2. rank, and stage the keys ------------------------------------
+        uint32_t* const cnt = s_wcnt + warp * RADIX;
+        uint32_t* const mask = smem + L::MASK + warp * RADIX;
+        uint32_t pos[ITEMS];
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const uint32_t li = wofs + j * 32 + lane;
-            if (li < valid) s_stage[rank[j]] = val[j];
+            const uint32_t live = prefix_lanes(wofs + j * 32, valid);
+            const bool is_live = li < valid;
+            const uint32_t k = in_k[li];
+            const uint32_t d = (k >> shift) & (RADIX - 1);
+            uint32_t peers;
+            if (j & 1) {
+                peers = match_label<RADIX_BITS>(d) & live;  // integer pipe
+            } else {
+                __syncwarp();                                // shared-memory pipe
+                if (is_live) atomicOr(&mask[d], 1u << lane);
+                __syncwarp();
+                peers = is_live ? mask[d] : 0u;
+                __syncwarp();
+                if (is_live && (peers & lt) == 0) mask[d] = 0;
+            }
+            const uint32_t first = __ffs(peers) - 1;
+            uint32_t before = 0;
+            if (lane == first) before = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+            before = __shfl_sync(0xffffffffu, before, first & 31u);
+            pos[j] = before + __popc(peers & lt);
+            if (is_live) s_stage[pos[j]] = k;
+        }
+        // This warp's counter row is done: clear it for the next tile's counts.
+        __syncwarp();
+        for (uint32_t i = lane; i < RADIX / 4; i += 32)
+            reinterpret_cast<uint4*>(cnt)[i] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+
+        // ---- 3. look-back (threads < 256) || count the next tile ------------
+        uint32_t next_id = 0;
+        if (tid < RADIX) {
+            S before_tile = 0;
+            if (tile > 0) {
+                int32_t t = (int32_t)tile - 1;
+                uint32_t spins = 0;
+                while (true) {
+                    S v[WIN];
+#pragma unroll
+                    for (int i = 0; i < WIN; ++i)
+                        v[i] = (t - i >= 0) ? ld_relaxed(status + (size_t)(t - i) * RADIX + tid)
+                                            : SW::INC;
+                    int used = 0;
+                    bool done = false;
+#pragma unroll
+                    for (int i = 0; i < WIN; ++i) {
+                        const S flag = v[i] & SW::FLAGS;
+                        if (flag == 0) break;  // not published yet: wait for this one
+                        before_tile += v[i] & SW::VALUE;
+                        used = i + 1;
+                        if (flag == SW::INC) {
+                            done = true;
+                            break;
+                        }
+                    }
+                    if (done) break;
+                    t -= used;
+                    if (used == WIN) continue;
+                    if (++spins > spin_limit) {
+                        record_error(ctrl, sticky, ERR_TIMEOUT);
+                        __threadfence();  // error visible before the INC below
+                        s_flag = 1;
+                        break;
+                    }
+                    if ((spins & 63u) == 0 && ld_relaxed(&ctrl->err) != 0) {
+                        s_flag = 1;
+                        break;
+                    }
+                }
+                st_relaxed(status + (size_t)tile * RADIX + tid,
+                           SW::INC | ((before_tile + (S)count) & SW::VALUE));
+            }
+            s_gofs[tid] = s_gbase[tid] + (uint32_t)before_tile - excl_in_tile;
+            if (tid == 0) {
+                if (s_err_seen) s_flag = 1;
+                // This CTA waits on no other CTA from here until the counts of
+                // the tile taken now are published: taking it cannot stall
+                // anyone.
+                next_id = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+            }
+        }
+        if (have_next) {
+            const uint32_t nvalid = tile_valid(nxt);
+            if (SPARE) {
+                if (warp >= LB_WARPS) {
+                    wait_bar(buf ^ 1);
+                    for (uint32_t w = warp - LB_WARPS; w < WARPS; w += WARPS - LB_WARPS)
+                        count_slots_of(buf ^ 1, nvalid, w);
+                } else {
+                    phase ^= 1u << (buf ^ 1);  // the count warps waited for it
+                }
+            } else {
+                wait_bar(buf ^ 1);
+                count_slots_of(buf ^ 1, nvalid, warp);
+            }
         }
         __syncthreads();
+        if (have_next) publish_counts(nxt);
+        if (s_flag) {
+            // An error somewhere: write nothing more.  The next tile's keys
+            // have landed; let this tile's values land too before exiting.
+            if (PAIRS) wait_bar(2);
+            break;
+        }
+
+        // ---- 4. stage the values, then fetch the next tile's ----------------
+        if (PAIRS) {
+            wait_bar(2);
+            uint32_t vv[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) vv[j] = s_in_v[wofs + j * 32 + lane];
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (wofs + j * 32 + lane < valid) in_k[pos[j]] = vv[j];
+            __syncthreads();
+            if (have_next) issue_copy(smem + L::IN_V, src_v, nxt, &s_bar[2]);
+        }
+
+        // ---- 5. coalesced stores of the bucket runs -------------------------
+        bool bad = false;
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k) {
             const uint32_t s = k * THREADS + tid;
-            if (s < valid && gpos[k] < n) dst_v[gpos[k]] = s_stage[s];
+            if (s < valid) {
+                const uint32_t kk = s_stage[s];
+                const uint32_t g = s_gofs[(kk >> shift) & (RADIX - 1)] + s;
+                if (g < n) {
+                    dst_k[g] = kk;
+                    if (PAIRS) dst_v[g] = in_k[s];
+                } else {
+                    bad = true;
+                }
+            }
         }
+        if (bad) record_error(ctrl, sticky, ERR_BOUNDS);
+        if (tid == 0) s_ids[(it + 2) & 3] = next_id;
+        __syncthreads();
     }
-    if (bad) record_error(ctrl, sticky, ERR_BOUNDS);
+    // Every bulk copy is waited for before the loop can end, so no copy is in
+    // flight into this CTA's shared memory when it exits.
 }
 
 }  // namespace rs

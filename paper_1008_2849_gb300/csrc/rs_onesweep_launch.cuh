@@ -7,27 +7,47 @@
 
 namespace rs {
 
-template <int THREADS, int ITEMS, bool PAIRS, typename S>
+// The tile shapes of kTileConfigs (rs_sort.cu), in the same order:
+// (index, threads, items per thread, CTAs per SM, look-back window).
+#define RS_TILE_SHAPES(X)   \
+    X(0, 512, 16, 1, 32)    \
+    X(1, 512, 8, 2, 16)     \
+    X(2, 256, 16, 2, 32)    \
+    X(3, 384, 12, 2, 16)    \
+    X(4, 768, 8, 1, 32)     \
+    X(5, 1024, 8, 1, 32)
+
+template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S>
 static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
                                        uint32_t n, uint32_t pass, Ctrl* ctrl, uint32_t* sticky,
                                        void* status, void* status_clear, cudaStream_t stream) {
-    constexpr uint32_t TILE = THREADS * ITEMS;
-    const size_t smem = TILE * sizeof(uint32_t);
-    auto kern = k_onesweep<THREADS, ITEMS, PAIRS, S>;
-    static uint64_t attr_set_on = 0;  // one bit per device that has the attribute
+    using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
+    constexpr uint32_t TILE = L::TILE;
+    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW>;
+    static int ctas_per_sm[64] = {0};  // per device: resident CTAs per SM
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
-    if (!((attr_set_on >> dev) & 1u)) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (ctas_per_sm[dev] == 0) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES) !=
             cudaSuccess)
             return RS_ERR_CUDA;
-        attr_set_on |= 1ull << dev;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, THREADS, L::BYTES) !=
+                cudaSuccess ||
+            blocks < 1)
+            return RS_ERR_CUDA;
+        ctas_per_sm[dev] = blocks;
     }
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
     const uint32_t tiles = (uint32_t)((n + (size_t)TILE - 1) / TILE);
+    uint32_t grid = (uint32_t)(di.sm_count * ctas_per_sm[dev]);
+    if (grid > tiles) grid = tiles;
     note_launch_begin(KK_ONESWEEP, stream);
-    kern<<<tiles, THREADS, smem, stream>>>(ka, va, kb, vb, n, pass, ctrl, sticky,
-                                           static_cast<S*>(status), static_cast<S*>(status_clear),
-                                           knobs().spin_limit, knobs().debug);
+    kern<<<grid, THREADS, L::BYTES, stream>>>(ka, va, kb, vb, n, pass, tiles, ctrl, sticky,
+                                              static_cast<S*>(status), static_cast<S*>(status_clear),
+                                              tiles * RADIX, knobs().spin_limit, knobs().debug);
     note_launch_end(KK_ONESWEEP, stream);
     return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
@@ -38,9 +58,12 @@ static rs_status launch_onesweep_typed(int cfg, uint32_t* ka, uint32_t* va, uint
                                        uint32_t* sticky, void* status, void* status_clear,
                                        cudaStream_t stream) {
     switch (cfg) {
-    case 0: return launch_onesweep_shape<256, 16, PAIRS, S>(ka, va, kb, vb, n, pass, ctrl, sticky, status, status_clear, stream);
-    case 1: return launch_onesweep_shape<512, 16, PAIRS, S>(ka, va, kb, vb, n, pass, ctrl, sticky, status, status_clear, stream);
-    case 2: return launch_onesweep_shape<512, 12, PAIRS, S>(ka, va, kb, vb, n, pass, ctrl, sticky, status, status_clear, stream);
+#define RS_CASE(I, T, J, B, W)                                                                    \
+    case I:                                                                                       \
+        return launch_onesweep_shape<T, J, B, W, PAIRS, S>(ka, va, kb, vb, n, pass, ctrl, sticky, \
+                                                           status, status_clear, stream);
+        RS_TILE_SHAPES(RS_CASE)
+#undef RS_CASE
     default: return RS_ERR_INVALID_ARG;
     }
 }

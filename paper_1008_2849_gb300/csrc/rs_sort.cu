@@ -5,7 +5,9 @@
 
 namespace rs {
 
-const TileConfig kTileConfigs[NUM_TILE_CONFIGS] = {{256, 16}, {512, 16}, {512, 12}};
+// Must list the shapes of RS_TILE_SHAPES (rs_onesweep_launch.cuh) in order.
+const TileConfig kTileConfigs[NUM_TILE_CONFIGS] = {{512, 16, 1}, {512, 8, 2}, {256, 16, 2},
+                                                   {384, 12, 2}, {768, 8, 1}, {1024, 8, 1}};
 
 int smallest_tile() {
     int t = kTileConfigs[0].threads * kTileConfigs[0].items;
@@ -48,9 +50,15 @@ static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, v
     const uint32_t needed = (vec4 + 63) / 64 / (HIST_THREADS / 32) + 1;  // 64 vectors per warp
     if (blocks > needed) blocks = needed;
     if (blocks < 1) blocks = 1;
+    auto kern = k_hist4<HIST_THREADS, HIST_LEADER>;
+    switch (knobs().hist_mode) {
+    case HIST_ATOMIC: kern = k_hist4<HIST_THREADS, HIST_ATOMIC>; break;
+    case HIST_MATCH: kern = k_hist4<HIST_THREADS, HIST_MATCH>; break;
+    default: break;
+    }
     note_launch_begin(KK_HIST, stream);
-    k_hist4<HIST_THREADS><<<blocks, HIST_THREADS, 0, stream>>>(
-        keys, n, hist, static_cast<uint4*>(clear), (uint32_t)(clear_bytes / sizeof(uint4)));
+    kern<<<blocks, HIST_THREADS, 0, stream>>>(keys, n, hist, static_cast<uint4*>(clear),
+                                              (uint32_t)(clear_bytes / sizeof(uint4)));
     note_launch_end(KK_HIST, stream);
     return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }

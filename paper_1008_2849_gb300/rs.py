@@ -47,6 +47,10 @@ SIGNATURES = {
     "rs_profile_enable": (_int, [_int]),
     "rs_profile_read": (_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), _int]),
     "rs_kernel_kind_name": (ctypes.c_char_p, [_int]),
+    "rs_tune_set": (_int, [_int, _int]),
+    "rs_tune_get": (_int, [_int]),
+    "rs_tile_shape_count": (_int, []),
+    "rs_tile_shape": (_int, [_int, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "rs_debug_set_spin_limit": (_int, [_u32]),
     "rs_debug_withhold_first_tile": (_int, [_int]),
 }
@@ -198,6 +202,27 @@ def profile_read() -> dict:
     for i in range(k):
         name = lib().rs_kernel_kind_name(i).decode()
         out[name] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+TUNE_KNOBS = {"tile_pairs": 0, "tile_keys": 1, "hist_ctas_per_sm": 2, "hist_mode": 3}
+
+
+def tune_set(knob: str, value: int) -> None:
+    _check(lib().rs_tune_set(TUNE_KNOBS[knob], int(value)), "rs_tune_set(%s)" % knob)
+
+
+def tune_get(knob: str) -> int:
+    return int(lib().rs_tune_get(TUNE_KNOBS[knob]))
+
+
+def tile_shapes():
+    """[(threads, items_per_thread)] of the compiled scatter-pass tile shapes."""
+    out = []
+    for i in range(int(lib().rs_tile_shape_count())):
+        t, j = _int(0), _int(0)
+        _check(lib().rs_tile_shape(i, ctypes.byref(t), ctypes.byref(j)), "rs_tile_shape")
+        out.append((t.value, j.value))
     return out
 
 
