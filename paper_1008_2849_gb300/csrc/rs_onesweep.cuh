@@ -6,6 +6,8 @@
 // Sec. 2.
 #pragma once
 
+#include <type_traits>
+
 #include "rs_device.cuh"
 
 namespace rs {
@@ -106,6 +108,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     const uint32_t* const s_in_v = smem + L::IN_V;
     __shared__ uint32_t s_gbase[RADIX];  // G[pass][b]
     __shared__ uint32_t s_gofs[RADIX];   // G + before_tile - tile_excl, per tile
+    __shared__ uint32_t s_cnt[RADIX];    // digit counts of the next tile to rank
     __shared__ uint32_t s_scan[RADIX / 32];
     __shared__ uint32_t s_ids[4];
     __shared__ uint32_t s_flag;
@@ -182,13 +185,17 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     const uint32_t wofs = warp * WARP_ITEMS;
     // Count the slots of warp w of the tile in key buffer b into wcnt row w.
     auto count_slots_of = [&](uint32_t b, uint32_t valid, uint32_t w) {
-        const uint32_t* keys = smem + L::IN_K + b * TILE;
+        const uint32_t* keys = smem + L::IN_K + b * TILE + w * WARP_ITEMS + lane;
         uint32_t* row = s_wcnt + w * RADIX;
-        const uint32_t base = w * WARP_ITEMS;
+        if (valid == TILE) {
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t li = base + j * 32 + lane;
-            if (li < valid) atomicAdd(&row[(keys[li] >> shift) & (RADIX - 1)], 1u);
+            for (int j = 0; j < ITEMS; ++j)
+                atomicAdd(&row[(keys[j * 32] >> shift) & (RADIX - 1)], 1u);
+        } else {
+            const uint32_t left = valid > w * WARP_ITEMS ? valid - w * WARP_ITEMS : 0u;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (j * 32 + lane < left) atomicAdd(&row[(keys[j * 32] >> shift) & (RADIX - 1)], 1u);
         }
     };
     // Publish the counts of tile t (per-warp counts in wcnt): AGG, or INC for
@@ -198,6 +205,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             uint32_t c = 0;
 #pragma unroll
             for (uint32_t w = 0; w < WARPS; ++w) c += s_wcnt[w * RADIX + tid];
+            s_cnt[tid] = c;  // the tile's counts, reused when the tile is ranked
             const bool withhold = (debug & DBG_WITHHOLD_FIRST_TILE) && t == 0;
             if (!withhold)
                 st_relaxed(status + (size_t)t * RADIX + tid, (t == 0 ? SW::INC : SW::AGG) | (S)c);
@@ -234,11 +242,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         uint32_t* const in_k = smem + L::IN_K + buf * TILE;
 
         // ---- 1. counts, prefix over digits, per-warp positions -----------
-        uint32_t count = 0;
-        if (tid < RADIX) {
-#pragma unroll
-            for (uint32_t w = 0; w < WARPS; ++w) count += s_wcnt[w * RADIX + tid];
-        }
+        const uint32_t count = tid < RADIX ? s_cnt[tid] : 0u;
         uint32_t x = count;
 #pragma unroll
         for (uint32_t o = 1; o < 32; o <<= 1) {
@@ -266,31 +270,39 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         uint32_t* const cnt = s_wcnt + warp * RADIX;
         uint32_t* const mask = smem + L::MASK + warp * RADIX;
         uint32_t pos[ITEMS];
+        auto rank_tile = [&](auto full) {
+            constexpr bool FULL = decltype(full)::value;
+            const uint32_t left = FULL ? WARP_ITEMS : (valid > wofs ? valid - wofs : 0u);
+            const uint32_t* keys = in_k + wofs + lane;
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t li = wofs + j * 32 + lane;
-            const uint32_t live = prefix_lanes(wofs + j * 32, valid);
-            const bool is_live = li < valid;
-            const uint32_t k = in_k[li];
-            const uint32_t d = (k >> shift) & (RADIX - 1);
-            uint32_t peers;
-            if (j & 1) {
-                peers = match_label<RADIX_BITS>(d) & live;  // integer pipe
-            } else {
-                __syncwarp();                                // shared-memory pipe
-                if (is_live) atomicOr(&mask[d], 1u << lane);
-                __syncwarp();
-                peers = is_live ? mask[d] : 0u;
-                __syncwarp();
-                if (is_live && (peers & lt) == 0) mask[d] = 0;
+            for (int j = 0; j < ITEMS; ++j) {
+                const bool is_live = FULL || j * 32 + lane < left;
+                const uint32_t live = FULL ? 0xffffffffu : prefix_lanes(j * 32, left);
+                const uint32_t k = keys[j * 32];
+                const uint32_t d = (k >> shift) & (RADIX - 1);
+                uint32_t peers;
+                if (j & 1) {
+                    peers = match_label<RADIX_BITS>(d) & live;  // integer pipe
+                } else {
+                    __syncwarp();                                // shared-memory pipe
+                    if (is_live) atomicOr(&mask[d], 1u << lane);
+                    __syncwarp();
+                    peers = is_live ? mask[d] : 0u;
+                    __syncwarp();
+                    if (is_live && (peers & lt) == 0) mask[d] = 0;
+                }
+                const uint32_t first = __ffs(peers) - 1;
+                uint32_t before = 0;
+                if (lane == first) before = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+                before = __shfl_sync(0xffffffffu, before, first & 31u);
+                pos[j] = before + __popc(peers & lt);
+                if (is_live) s_stage[pos[j]] = k;
             }
-            const uint32_t first = __ffs(peers) - 1;
-            uint32_t before = 0;
-            if (lane == first) before = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
-            before = __shfl_sync(0xffffffffu, before, first & 31u);
-            pos[j] = before + __popc(peers & lt);
-            if (is_live) s_stage[pos[j]] = k;
-        }
+        };
+        if (valid == TILE)
+            rank_tile(std::true_type{});
+        else
+            rank_tile(std::false_type{});
         // This warp's counter row is done: clear it for the next tile's counts.
         __syncwarp();
         for (uint32_t i = lane; i < RADIX / 4; i += 32)
@@ -305,18 +317,18 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 int32_t t = (int32_t)tile - 1;
                 uint32_t spins = 0;
                 while (true) {
-                    S v[WIN];
+                    S lb[WIN];
 #pragma unroll
                     for (int i = 0; i < WIN; ++i)
-                        v[i] = (t - i >= 0) ? ld_relaxed(status + (size_t)(t - i) * RADIX + tid)
-                                            : SW::INC;
+                        lb[i] = (t - i >= 0) ? ld_relaxed(status + (size_t)(t - i) * RADIX + tid)
+                                             : SW::INC;
                     int used = 0;
                     bool done = false;
 #pragma unroll
                     for (int i = 0; i < WIN; ++i) {
-                        const S flag = v[i] & SW::FLAGS;
+                        const S flag = lb[i] & SW::FLAGS;
                         if (flag == 0) break;  // not published yet: wait for this one
-                        before_tile += v[i] & SW::VALUE;
+                        before_tile += lb[i] & SW::VALUE;
                         used = i + 1;
                         if (flag == SW::INC) {
                             done = true;
@@ -379,29 +391,41 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             uint32_t vv[ITEMS];
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) vv[j] = s_in_v[wofs + j * 32 + lane];
+            if (valid == TILE) {
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j)
-                if (wofs + j * 32 + lane < valid) in_k[pos[j]] = vv[j];
+                for (int j = 0; j < ITEMS; ++j) in_k[pos[j]] = vv[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j)
+                    if (wofs + j * 32 + lane < valid) in_k[pos[j]] = vv[j];
+            }
             __syncthreads();
             if (have_next) issue_copy(smem + L::IN_V, src_v, nxt, &s_bar[2]);
         }
 
         // ---- 5. coalesced stores of the bucket runs -------------------------
         bool bad = false;
+        auto scatter_tile = [&](auto full) {
+            constexpr bool FULL = decltype(full)::value;
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            const uint32_t s = k * THREADS + tid;
-            if (s < valid) {
-                const uint32_t kk = s_stage[s];
-                const uint32_t g = s_gofs[(kk >> shift) & (RADIX - 1)] + s;
-                if (g < n) {
-                    dst_k[g] = kk;
-                    if (PAIRS) dst_v[g] = in_k[s];
-                } else {
-                    bad = true;
+            for (int k = 0; k < ITEMS; ++k) {
+                const uint32_t s = k * THREADS + tid;
+                if (FULL || s < valid) {
+                    const uint32_t kk = s_stage[s];
+                    const uint32_t g = s_gofs[(kk >> shift) & (RADIX - 1)] + s;
+                    if (g < n) {
+                        dst_k[g] = kk;
+                        if (PAIRS) dst_v[g] = in_k[s];
+                    } else {
+                        bad = true;
+                    }
                 }
             }
-        }
+        };
+        if (valid == TILE)
+            scatter_tile(std::true_type{});
+        else
+            scatter_tile(std::false_type{});
         if (bad) record_error(ctrl, sticky, ERR_BOUNDS);
         if (tid == 0) s_ids[(it + 2) & 3] = next_id;
         __syncthreads();
