@@ -108,6 +108,37 @@ rs_status rs_digit_histograms_ex(const uint32_t* d_keys, size_t n, uint32_t* d_h
 rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in,
                              uint32_t* h_keys_out, uint32_t* h_vals_out, size_t n);
 
+/* ---- sorting without allocating ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory when they sort: code on a
+ * latency-critical path (cudaMalloc and cudaFree can synchronise the whole
+ * device and stall every stream in flight), and processes that hand all of
+ * the device memory to their own pool or arena, where an extra cudaMalloc
+ * may fail.  rs_sort_keys / rs_sort_pairs allocate a cached workspace on
+ * first use, and the _ex calls need a caller-provided one; this call needs
+ * neither. */
+
+/* Largest n accepted by rs_sort_pairs_noalloc (2^20 items). */
+#define RS_NOALLOC_MAX_ITEMS (1u << 20)
+
+/* Sort n keys (d_vals == NULL) or n (key, value) pairs in place, exactly as
+ * rs_sort_pairs does, enqueued on cuda_stream (NULL = legacy default stream)
+ * without allocating anything: no cudaMalloc, cudaFree or allocating library
+ * call is made.  The scratch is a fixed 9 MiB array inside librs.so that
+ * every GPU loading the library holds until the process exits.
+ *  - n > RS_NOALLOC_MAX_ITEMS returns RS_ERR_UNSUPPORTED before any work.
+ *  - Asynchronous: the caller collects device-side errors with
+ *    rs_stream_status().
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array (each call clears what must
+ *    start at zero), so calls whose work overlaps on the GPU -- two streams,
+ *    or two host threads -- race and corrupt each other's results; order
+ *    them on one stream or synchronise in between. */
+rs_status rs_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                                void* cuda_stream);
+
 /* ---- instrumentation (used by the benchmark; off by default) ---------- */
 
 /* Number of kernels this library has launched on any device since it was

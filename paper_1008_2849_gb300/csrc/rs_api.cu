@@ -88,18 +88,6 @@ rs_status device_info_for(int dev, DeviceInfo* out) {
     return RS_OK;
 }
 
-rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n) {
-    if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
-    if (n > 0 && keys == nullptr) return RS_ERR_INVALID_ARG;
-    if (vals != nullptr && n > 0) {
-        const uintptr_t k0 = (uintptr_t)keys, k1 = k0 + n * 4;
-        const uintptr_t v0 = (uintptr_t)vals, v1 = v0 + n * 4;
-        if (k0 < v1 && v0 < k1) return RS_ERR_INVALID_ARG;  // overlapping
-    }
-    if (((uintptr_t)keys & 3u) || ((uintptr_t)vals & 3u)) return RS_ERR_INVALID_ARG;
-    return RS_OK;
-}
-
 rs_status ensure_workspace_locked(DevState& d, size_t bytes) {
     if (d.ws_bytes >= bytes) return RS_OK;
     if (d.ws) cudaFree(d.ws);
@@ -150,6 +138,18 @@ rs_status plain_sort(uint32_t* keys, uint32_t* vals, size_t n) {
 }
 
 }  // namespace
+
+rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n) {
+    if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
+    if (n > 0 && keys == nullptr) return RS_ERR_INVALID_ARG;
+    if (vals != nullptr && n > 0) {
+        const uintptr_t k0 = (uintptr_t)keys, k1 = k0 + n * 4;
+        const uintptr_t v0 = (uintptr_t)vals, v1 = v0 + n * 4;
+        if (k0 < v1 && v0 < k1) return RS_ERR_INVALID_ARG;  // overlapping
+    }
+    if (((uintptr_t)keys & 3u) || ((uintptr_t)vals & 3u)) return RS_ERR_INVALID_ARG;
+    return RS_OK;
+}
 
 Knobs& knobs() {
     static Knobs k{3, 3, kDefaultSpinLimit, 0, 4, 0};

@@ -47,6 +47,10 @@ struct Knobs {
 };
 Knobs& knobs();
 
+// Host-side checks shared by the sort entry points: size, null pointers,
+// 4-byte alignment, keys and values not overlapping.
+rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n);
+
 // Per-device facts cached on first use.
 struct DeviceInfo {
     int sm_count;

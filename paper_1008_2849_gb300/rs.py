@@ -43,6 +43,7 @@ SIGNATURES = {
     "rs_status_string": (ctypes.c_char_p, [_int]),
     "rs_digit_histograms_ex": (_int, [_vp, _sz, _vp, _vp]),
     "rs_sort_pairs_host": (_int, [_vp, _vp, _vp, _vp, _sz]),
+    "rs_sort_pairs_noalloc": (_int, [_vp, _vp, _sz, _vp]),
     "rs_launch_count": (ctypes.c_uint64, []),
     "rs_profile_enable": (_int, [_int]),
     "rs_profile_read": (_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), _int]),
@@ -183,6 +184,23 @@ def sort_pairs_host(keys_in, vals_in, keys_out, vals_out) -> None:
     n = keys_in.numel() if hasattr(keys_in, "numel") else keys_in.size
     _check(lib().rs_sort_pairs_host(hp(keys_in), hp(vals_in), hp(keys_out), hp(vals_out), n),
            "rs_sort_pairs_host")
+
+
+NOALLOC_MAX_ITEMS = 1 << 20
+
+
+def sort_pairs_noalloc(keys, vals=None, stream=None) -> None:
+    """Enqueue an in-place sort that allocates no device memory (n <= 2^20).
+
+    For callers that must not allocate at call time.  Uses a fixed scratch
+    array inside librs.so shared by all calls on a device: calls that overlap
+    on the GPU race.  Asynchronous; collect errors with stream_status()."""
+    if vals is not None and vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    _check(lib().rs_sort_pairs_noalloc(_dev_ptr(keys, "keys"),
+                                       None if vals is None else _dev_ptr(vals, "vals"),
+                                       keys.numel(), _stream_handle(stream)),
+           "rs_sort_pairs_noalloc")
 
 
 def launch_count() -> int:
