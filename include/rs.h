@@ -79,6 +79,32 @@ rs_status rs_sort_keys_ex(uint32_t* d_keys, size_t n,
 rs_status rs_sort_pairs_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n,
                            void* cuda_stream, void* d_workspace, size_t workspace_bytes);
 
+/* Segmented sorts: every segment [d_offsets[s], d_offsets[s+1]) of the n-item
+ * array, s = 0..num_segments-1, is sorted on its own, stably and ascending,
+ * exactly as if it were a separate array (the paper has no segmented case;
+ * this is its sort applied per segment).  d_offsets is a device array of
+ * num_segments + 1 nondecreasing uint32 entries with d_offsets[num_segments]
+ * <= n; segments may be empty; items outside [d_offsets[0],
+ * d_offsets[num_segments]) are left as they are; a single segment must hold
+ * fewer than 2^30 items.  A table that breaks these rules is detected on the
+ * device: nothing is written and the status is RS_ERR_BAD_SEGMENTS.
+ * Segments of at most 4096 items (or the RS_TUNE_SMALL_MAX setting, up to
+ * 8192) are sorted by one CTA each in shared memory; larger ones by the
+ * four scatter passes of the unsegmented sort, all large segments together.
+ * Plain forms are synchronous; _ex forms as above, with
+ * workspace_bytes >= rs_workspace_bytes(n, with_values, num_segments). */
+rs_status rs_sort_keys_segmented(uint32_t* d_keys, size_t n, const uint32_t* d_offsets,
+                                 uint32_t num_segments);
+rs_status rs_sort_pairs_segmented(uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                                  const uint32_t* d_offsets, uint32_t num_segments);
+rs_status rs_sort_keys_segmented_ex(uint32_t* d_keys, size_t n, const uint32_t* d_offsets,
+                                    uint32_t num_segments, void* cuda_stream,
+                                    void* d_workspace, size_t workspace_bytes);
+rs_status rs_sort_pairs_segmented_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                                     const uint32_t* d_offsets, uint32_t num_segments,
+                                     void* cuda_stream, void* d_workspace,
+                                     size_t workspace_bytes);
+
 /* Bytes of device workspace an _ex call needs.  n = total items; with_values
  * = 0 for keys only, 1 for pairs; num_segments = 0 for the unsegmented calls,
  * else the number of segments of a segmented call.  Pure host arithmetic. */
@@ -166,7 +192,10 @@ typedef enum rs_tune_knob {
     RS_TUNE_TILE_PAIRS = 0,       /* tile shape index (rs_tile_shape) of key-value passes */
     RS_TUNE_TILE_KEYS = 1,        /* tile shape index of keys-only passes */
     RS_TUNE_HIST_CTAS_PER_SM = 2, /* CTAs per SM of the histogram kernel, 1..16 */
-    RS_TUNE_HIST_MODE = 3         /* 0: lane atomics, 1: lane-0 group + atomics, 2: ballot groups */
+    RS_TUNE_HIST_MODE = 3,        /* 0: lane atomics, 1: lane-0 group + atomics, 2: ballot groups */
+    RS_TUNE_SMALL_MAX = 4,        /* arrays and segments up to this size (<= 8192) take the
+                                     one-CTA shared-memory sort; segments up to 4096 always do */
+    RS_TUNE_TILE_SEG = 5          /* tile shape index of the segmented scatter passes */
 } rs_tune_knob;
 
 /* Set a knob; RS_ERR_INVALID_ARG for an unknown knob or out-of-range value. */

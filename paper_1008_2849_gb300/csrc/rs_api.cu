@@ -152,7 +152,7 @@ rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n) 
 }
 
 Knobs& knobs() {
-    static Knobs k{3, 3, kDefaultSpinLimit, 0, 4, 0};
+    static Knobs k{3, 3, kDefaultSpinLimit, 0, 4, 0, 4096, 3};
     return k;
 }
 
@@ -161,6 +161,11 @@ const char* kernel_kind_name(int kind) {
     case KK_HIST: return "hist4";
     case KK_PLAN: return "plan";
     case KK_ONESWEEP: return "onesweep";
+    case KK_SMALL: return "small_sort";
+    case KK_SEG_PLAN: return "seg_plan";
+    case KK_SEG_HIST: return "seg_hist";
+    case KK_SEG_SCAN: return "seg_scan";
+    case KK_SEG_ONESWEEP: return "seg_onesweep";
     default: return nullptr;
     }
 }
@@ -222,9 +227,74 @@ rs_status rs_sort_pairs_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n, void* c
     return ex_sort(d_keys, d_vals, n, cuda_stream, d_workspace, workspace_bytes);
 }
 
+static rs_status seg_args(const uint32_t* keys, const uint32_t* vals, size_t n,
+                          const uint32_t* offsets, uint32_t num_segments) {
+    rs_status st = check_sort_args(keys, vals, n);
+    if (st != RS_OK) return st;
+    if (num_segments > 0 && offsets == nullptr) return RS_ERR_INVALID_ARG;
+    if (((uintptr_t)offsets & 3u)) return RS_ERR_INVALID_ARG;
+    return RS_OK;
+}
+
+static rs_status plain_segmented(uint32_t* keys, uint32_t* vals, size_t n,
+                                 const uint32_t* offsets, uint32_t num_segments) {
+    rs_status st = seg_args(keys, vals, n, offsets, num_segments);
+    if (st != RS_OK || n == 0 || num_segments == 0) return st;
+    std::lock_guard<std::mutex> lock(g_mu);
+    const int dev = current_device();
+    if (dev < 0) return RS_ERR_CUDA;
+    DeviceInfo di;
+    st = device_info_for(dev, &di);
+    if (st != RS_OK) return st;
+    DevState& d = g_dev[dev];
+    st = ensure_workspace_locked(d, seg_layout_for(n, vals != nullptr, num_segments).total);
+    if (st != RS_OK) return st;
+    st = enqueue_sort_segmented(keys, vals, (uint32_t)n, offsets, num_segments, cudaStreamLegacy,
+                                d.ws, d.ws_bytes);
+    if (st != RS_OK) return st;
+    return sticky_status(cudaStreamLegacy);
+}
+
+rs_status rs_sort_keys_segmented(uint32_t* d_keys, size_t n, const uint32_t* d_offsets,
+                                 uint32_t num_segments) {
+    return plain_segmented(d_keys, nullptr, n, d_offsets, num_segments);
+}
+
+rs_status rs_sort_pairs_segmented(uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                                  const uint32_t* d_offsets, uint32_t num_segments) {
+    if (n > 0 && d_vals == nullptr) return RS_ERR_INVALID_ARG;
+    return plain_segmented(d_keys, d_vals, n, d_offsets, num_segments);
+}
+
+static rs_status ex_segmented(uint32_t* keys, uint32_t* vals, size_t n, const uint32_t* offsets,
+                              uint32_t num_segments, void* stream, void* ws, size_t ws_bytes) {
+    rs_status st = seg_args(keys, vals, n, offsets, num_segments);
+    if (st != RS_OK || n == 0 || num_segments == 0) return st;
+    if (ws == nullptr || ws_bytes < seg_layout_for(n, vals != nullptr, num_segments).total)
+        return RS_ERR_INVALID_ARG;
+    return enqueue_sort_segmented(keys, vals, (uint32_t)n, offsets, num_segments,
+                                  static_cast<cudaStream_t>(stream), ws, ws_bytes);
+}
+
+rs_status rs_sort_keys_segmented_ex(uint32_t* d_keys, size_t n, const uint32_t* d_offsets,
+                                    uint32_t num_segments, void* cuda_stream, void* d_workspace,
+                                    size_t workspace_bytes) {
+    return ex_segmented(d_keys, nullptr, n, d_offsets, num_segments, cuda_stream, d_workspace,
+                        workspace_bytes);
+}
+
+rs_status rs_sort_pairs_segmented_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                                     const uint32_t* d_offsets, uint32_t num_segments,
+                                     void* cuda_stream, void* d_workspace,
+                                     size_t workspace_bytes) {
+    if (n > 0 && d_vals == nullptr) return RS_ERR_INVALID_ARG;
+    return ex_segmented(d_keys, d_vals, n, d_offsets, num_segments, cuda_stream, d_workspace,
+                        workspace_bytes);
+}
+
 size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments) {
-    (void)num_segments;
     if (n == 0) return 0;
+    if (num_segments > 0) return seg_layout_for(n, with_values != 0, num_segments).total;
     return layout_for(n, with_values != 0).total;
 }
 
@@ -367,6 +437,14 @@ rs_status rs_tune_set(int knob, int value) {
         if (value < 0 || value > 2) return RS_ERR_INVALID_ARG;
         k.hist_mode = value;
         return RS_OK;
+    case 4:
+        if (value < 0 || value > (int)small_sort_capacity()) return RS_ERR_INVALID_ARG;
+        k.small_max = value;
+        return RS_OK;
+    case 5:
+        if (value < 0 || value >= NUM_TILE_CONFIGS) return RS_ERR_INVALID_ARG;
+        k.tile_config_seg = value;
+        return RS_OK;
     default: return RS_ERR_INVALID_ARG;
     }
 }
@@ -378,6 +456,8 @@ int rs_tune_get(int knob) {
     case 1: return k.tile_config_keys;
     case 2: return k.hist_ctas_per_sm;
     case 3: return k.hist_mode;
+    case 4: return k.small_max;
+    case 5: return k.tile_config_seg;
     default: return -1;
     }
 }

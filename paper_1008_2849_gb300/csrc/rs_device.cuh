@@ -35,7 +35,10 @@ struct Ctrl {
     uint32_t err;                  // error bits of this call
     uint32_t tile_ctr[PASSES];     // dynamic tile ids, one counter per pass
     uint32_t dir[PASSES];          // pass plan
-    uint32_t pad[7];               // keep hist 64-byte aligned
+    uint32_t seg_tiles;            // segmented sorts: tiles of the large segments
+    uint32_t small_count;          // segmented sorts: number of small segments
+    uint32_t large_count;          // segmented sorts: number of large segments
+    uint32_t pad[4];               // keep hist 64-byte aligned
     uint32_t hist[PASSES][RADIX];  // digit histograms (H)
     uint32_t gofs[PASSES][RADIX];  // first output slot of every bucket (G)
 };

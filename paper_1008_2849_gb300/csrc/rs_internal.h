@@ -18,6 +18,11 @@ enum KernelKind : int {
     KK_HIST = 0,
     KK_PLAN = 1,
     KK_ONESWEEP = 2,
+    KK_SMALL = 3,
+    KK_SEG_PLAN = 4,
+    KK_SEG_HIST = 5,
+    KK_SEG_SCAN = 6,
+    KK_SEG_ONESWEEP = 7,
     KK_COUNT
 };
 const char* kernel_kind_name(int kind);
@@ -44,6 +49,8 @@ struct Knobs {
     uint32_t debug;          // DBG_* bits
     int hist_ctas_per_sm;
     int hist_mode;           // HIST_ATOMIC / HIST_LEADER / HIST_MATCH
+    int small_max;           // segments (and whole sorts) up to this size use the one-CTA sort
+    int tile_config_seg;     // tile shape of the segmented scatter passes
 };
 Knobs& knobs();
 
@@ -75,14 +82,42 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
 rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
                              cudaStream_t stream);
 
-// Scatter-pass launchers, one per value flavour (separate translation units).
+// Segmented scatter passes: per-tile geometry and per-segment bucket bases
+// built on the device, and an upper bound of the tile count for the launch.
+struct SegView {
+    const uint4* tile_geo = nullptr;
+    const uint32_t* gofs = nullptr;
+    uint32_t max_tiles = 0;
+};
+
+// Scatter-pass launchers, one per value flavour (separate translation units);
+// seg == nullptr for the unsegmented sort.
 rs_status launch_onesweep_keys(int cfg, bool wide, uint32_t* ka, uint32_t* kb, uint32_t n,
                                uint32_t pass, Ctrl* ctrl, uint32_t* sticky, void* status,
-                               void* status_clear, cudaStream_t stream);
+                               void* status_clear, const SegView* seg, cudaStream_t stream);
 rs_status launch_onesweep_pairs(int cfg, bool wide, uint32_t* ka, uint32_t* va, uint32_t* kb,
                                 uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
                                 uint32_t* sticky, void* status, void* status_clear,
-                                cudaStream_t stream);
+                                const SegView* seg, cudaStream_t stream);
+
+// One-CTA sort in shared memory: of every small segment listed by the
+// segmented planner (off != nullptr), or of the single array [0, single_n)
+// with single_n <= small_sort_capacity().
+rs_status launch_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                            const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
+                            uint32_t max_items, cudaStream_t stream);
+uint32_t small_sort_capacity();
+
+// Workspace layout of a segmented sort of n items in num_segments segments.
+struct SegLayout {
+    size_t ctrl, status0, status1, alt_keys, alt_vals, tile_geo, small_list, large_first, gofs,
+        total;
+    uint32_t max_tiles, max_large;
+};
+SegLayout seg_layout_for(size_t n, bool pairs, uint32_t num_segments);
+rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
+                                 const uint32_t* offsets, uint32_t num_segments,
+                                 cudaStream_t stream, void* workspace, size_t workspace_bytes);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -82,13 +82,18 @@ struct OnesweepSmem {
 //     so consecutive threads store consecutive addresses of one bucket run.
 //     Every global store is checked against n (ERR_BOUNDS instead of a fault).
 // ---------------------------------------------------------------------------
-template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WINDOW>
+// Segmented sorts (SEG): tiles never straddle a segment.  tile_geo[t] =
+// (first item, item count, first tile of its segment, segment) for every tile
+// of the large segments; seg_gofs[s][pass][b] is the absolute first output
+// slot of bucket b of segment s; the number of tiles is ctrl->seg_tiles.
+template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WINDOW, bool SEG>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
            uint32_t* __restrict__ kb, uint32_t* __restrict__ vb,
            uint32_t n, uint32_t pass, uint32_t num_tiles, Ctrl* __restrict__ ctrl,
            uint32_t* __restrict__ sticky, S* __restrict__ status, S* __restrict__ status_clear,
-           uint32_t clear_words, uint32_t spin_limit, uint32_t debug) {
+           uint32_t clear_words, uint32_t spin_limit, uint32_t debug,
+           const uint4* __restrict__ tile_geo, const uint32_t* __restrict__ seg_gofs) {
     using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
     using SW = StatusWord<S>;
     static_assert(THREADS >= (int)RADIX && THREADS % 32 == 0, "one thread per digit");
@@ -111,12 +116,17 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     __shared__ uint32_t s_cnt[RADIX];    // digit counts of the next tile to rank
     __shared__ uint32_t s_scan[RADIX / 32];
     __shared__ uint32_t s_ids[4];
+    __shared__ uint4 s_geo[4];  // segmented: geometry of the tiles in s_ids
     __shared__ uint32_t s_flag;
     __shared__ uint32_t s_err_seen;  // the call's error word, read once per tile
     __shared__ __align__(8) uint64_t s_bar[3];  // key buffers 0 and 1, values
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+    if (SEG) {
+        if (ld_relaxed(&ctrl->err) != 0) return;  // malformed segment table: no work
+        num_tiles = ctrl->seg_tiles;
+    }
     const uint32_t dir = ctrl->dir[pass];
     if (dir == DIR_SKIP) {
         // No tiles in this pass: clear the whole next status array here.
@@ -132,25 +142,36 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
 
     for (uint32_t i = tid; i < 2 * WARPS * RADIX / 4; i += THREADS)
         reinterpret_cast<uint4*>(s_wcnt)[i] = make_uint4(0, 0, 0, 0);  // wcnt and mask
-    if (tid < RADIX) s_gbase[tid] = ctrl->gofs[pass][tid];
+    if (!SEG && tid < RADIX) s_gbase[tid] = ctrl->gofs[pass][tid];
+    // Geometry of tile t: (first item, item count, first tile of its segment,
+    // segment).
+    auto load_geo = [&](uint32_t t) -> uint4 {
+        if (SEG) return t < num_tiles ? tile_geo[t] : make_uint4(0, 0, 0, 0);
+        const uint32_t base = t * TILE;
+        return make_uint4(base, (n - base) < TILE ? (n - base) : TILE, 0u, 0u);
+    };
     if (tid == 0) {
         for (int b = 0; b < 3; ++b) mbar_init(&s_bar[b], 1);
         fence_mbar_init();
         s_ids[0] = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+        s_geo[0] = load_geo(s_ids[0]);
         s_flag = 0;
         s_err_seen = 0;
     }
     __syncthreads();
 
-    auto tile_valid = [&](uint32_t t) { return (n - t * TILE) < TILE ? (n - t * TILE) : TILE; };
-
-    // Start copying the `valid` items at src + t*TILE into dst (collective):
-    // one bulk copy of the 16-byte-aligned prefix, per-thread copies for the
-    // rest, all completing on `bar`.
-    auto issue_copy = [&](uint32_t* dst, const uint32_t* src, uint32_t t, uint64_t* bar) {
-        const uint32_t valid = tile_valid(t);
-        const uint32_t* from = src + (size_t)t * TILE;
-        const uint32_t nb = ((uintptr_t)from & 15u) == 0 ? (valid & ~3u) : 0u;
+    // Start copying the g.y items from src + g.x into dst (collective): the
+    // 16-byte-aligned middle by one bulk copy, the few items before and after
+    // it by per-thread copies, all completing on `bar`.
+    auto issue_copy = [&](uint32_t* dst, const uint32_t* src, uint4 g, uint64_t* bar) {
+        const uint32_t valid = g.y;
+        const uint32_t* from = src + g.x;
+        // Items before the first 16-byte boundary of the source; the bulk copy
+        // needs the same alignment on both sides, so it is used only when the
+        // destination offset agrees.
+        const uint32_t head = (uint32_t)((16u - ((uintptr_t)from & 15u)) & 15u) >> 2;
+        const bool bulk_ok = head == 0 && valid >= 4;
+        const uint32_t nb = bulk_ok ? (valid & ~3u) : 0u;
         if (nb < valid) {  // CTA-uniform
             bool issued = false;
             for (uint32_t i = nb + tid; i < valid; i += THREADS) {
@@ -200,7 +221,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     };
     // Publish the counts of tile t (per-warp counts in wcnt): AGG, or INC for
     // tile 0.
-    auto publish_counts = [&](uint32_t t) {
+    auto publish_counts = [&](uint32_t t, uint32_t first) {
         if (tid < RADIX) {
             uint32_t c = 0;
 #pragma unroll
@@ -208,20 +229,23 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             s_cnt[tid] = c;  // the tile's counts, reused when the tile is ranked
             const bool withhold = (debug & DBG_WITHHOLD_FIRST_TILE) && t == 0;
             if (!withhold)
-                st_relaxed(status + (size_t)t * RADIX + tid, (t == 0 ? SW::INC : SW::AGG) | (S)c);
+                st_relaxed(status + (size_t)t * RADIX + tid, (t == first ? SW::INC : SW::AGG) | (S)c);
         }
     };
 
     // Prologue: the first tile's data and counts; the second tile's id is taken
     // once they are published.
     if (s_ids[0] >= num_tiles) return;
-    issue_copy(smem + L::IN_K, src_k, s_ids[0], &s_bar[0]);
-    if (PAIRS) issue_copy(smem + L::IN_V, src_v, s_ids[0], &s_bar[2]);
+    issue_copy(smem + L::IN_K, src_k, s_geo[0], &s_bar[0]);
+    if (PAIRS) issue_copy(smem + L::IN_V, src_v, s_geo[0], &s_bar[2]);
     wait_bar(0);
-    count_slots_of(0, tile_valid(s_ids[0]), warp);
+    count_slots_of(0, s_geo[0].y, warp);
     __syncthreads();
-    publish_counts(s_ids[0]);
-    if (tid == 0) s_ids[1] = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+    publish_counts(s_ids[0], s_geo[0].z);
+    if (tid == 0) {
+        s_ids[1] = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+        s_geo[1] = load_geo(s_ids[1]);
+    }
     __syncthreads();
 
     const uint32_t lt = lanemask_lt();
@@ -231,14 +255,20 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         if (tile >= num_tiles) break;
         const uint32_t buf = it & 1;
         const uint32_t nxt = s_ids[(it + 1) & 3];
+        const uint4 geo = s_geo[it & 3];
+        const uint4 ngeo = s_geo[(it + 1) & 3];
         const bool have_next = nxt < num_tiles;
-        if (have_next) issue_copy(smem + L::IN_K + (buf ^ 1) * TILE, src_k, nxt, &s_bar[buf ^ 1]);
+        if (have_next) issue_copy(smem + L::IN_K + (buf ^ 1) * TILE, src_k, ngeo, &s_bar[buf ^ 1]);
+        // Segmented: this tile's bucket bases, fetched now, used after ranking.
+        uint32_t seg_base = 0;
+        if (SEG && tid < RADIX) seg_base = seg_gofs[((size_t)geo.w * PASSES + pass) * RADIX + tid];
         if (tid == ISSUER) s_err_seen = ld_relaxed(&ctrl->err);
         if (status_clear != nullptr)
             for (uint32_t b = tid; b < RADIX; b += THREADS)
                 status_clear[(size_t)tile * RADIX + b] = 0;
 
-        const uint32_t valid = tile_valid(tile);
+        const uint32_t valid = geo.y;
+        const uint32_t first_tile = geo.z;  // look-back stops here
         uint32_t* const in_k = smem + L::IN_K + buf * TILE;
 
         // ---- 1. counts, prefix over digits, per-warp positions -----------
@@ -311,17 +341,19 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
 
         // ---- 3. look-back (threads < 256) || count the next tile ------------
         uint32_t next_id = 0;
+        uint4 next_geo = make_uint4(0, 0, 0, 0);
         if (tid < RADIX) {
             S before_tile = 0;
-            if (tile > 0) {
+            if (tile > first_tile) {
                 int32_t t = (int32_t)tile - 1;
+                const int32_t lo = (int32_t)first_tile;
                 uint32_t spins = 0;
                 while (true) {
                     S lb[WIN];
 #pragma unroll
                     for (int i = 0; i < WIN; ++i)
-                        lb[i] = (t - i >= 0) ? ld_relaxed(status + (size_t)(t - i) * RADIX + tid)
-                                             : SW::INC;
+                        lb[i] = (t - i >= lo) ? ld_relaxed(status + (size_t)(t - i) * RADIX + tid)
+                                              : SW::INC;
                     int used = 0;
                     bool done = false;
 #pragma unroll
@@ -352,17 +384,18 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 st_relaxed(status + (size_t)tile * RADIX + tid,
                            SW::INC | ((before_tile + (S)count) & SW::VALUE));
             }
-            s_gofs[tid] = s_gbase[tid] + (uint32_t)before_tile - excl_in_tile;
+            s_gofs[tid] = (SEG ? seg_base : s_gbase[tid]) + (uint32_t)before_tile - excl_in_tile;
             if (tid == 0) {
                 if (s_err_seen) s_flag = 1;
                 // This CTA waits on no other CTA from here until the counts of
                 // the tile taken now are published: taking it cannot stall
                 // anyone.
                 next_id = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+                next_geo = load_geo(next_id);
             }
         }
         if (have_next) {
-            const uint32_t nvalid = tile_valid(nxt);
+            const uint32_t nvalid = ngeo.y;
             if (SPARE) {
                 if (warp >= LB_WARPS) {
                     wait_bar(buf ^ 1);
@@ -377,7 +410,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             }
         }
         __syncthreads();
-        if (have_next) publish_counts(nxt);
+        if (have_next) publish_counts(nxt, ngeo.z);
         if (s_flag) {
             // An error somewhere: write nothing more.  The next tile's keys
             // have landed; let this tile's values land too before exiting.
@@ -400,7 +433,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                     if (wofs + j * 32 + lane < valid) in_k[pos[j]] = vv[j];
             }
             __syncthreads();
-            if (have_next) issue_copy(smem + L::IN_V, src_v, nxt, &s_bar[2]);
+            if (have_next) issue_copy(smem + L::IN_V, src_v, ngeo, &s_bar[2]);
         }
 
         // ---- 5. coalesced stores of the bucket runs -------------------------
@@ -427,7 +460,10 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         else
             scatter_tile(std::false_type{});
         if (bad) record_error(ctrl, sticky, ERR_BOUNDS);
-        if (tid == 0) s_ids[(it + 2) & 3] = next_id;
+        if (tid == 0) {
+            s_ids[(it + 2) & 3] = next_id;
+            s_geo[(it + 2) & 3] = next_geo;
+        }
         __syncthreads();
     }
     // Every bulk copy is waited for before the loop can end, so no copy is in

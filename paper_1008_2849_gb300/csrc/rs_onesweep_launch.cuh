@@ -17,13 +17,14 @@ namespace rs {
     X(4, 768, 8, 1, 32)     \
     X(5, 1024, 8, 1, 32)
 
-template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S>
+template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S, bool SEG>
 static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
                                        uint32_t n, uint32_t pass, Ctrl* ctrl, uint32_t* sticky,
-                                       void* status, void* status_clear, cudaStream_t stream) {
+                                       void* status, void* status_clear, const SegView& seg,
+                                       cudaStream_t stream) {
     using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
     constexpr uint32_t TILE = L::TILE;
-    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW>;
+    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW, SEG>;
     static int ctas_per_sm[64] = {0};  // per device: resident CTAs per SM
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
@@ -41,27 +42,31 @@ static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb,
     DeviceInfo di;
     rs_status st = device_info(&di);
     if (st != RS_OK) return st;
-    const uint32_t tiles = (uint32_t)((n + (size_t)TILE - 1) / TILE);
+    // Segmented: the tile count is only known on the device (ctrl->seg_tiles).
+    const uint32_t tiles = SEG ? seg.max_tiles : (uint32_t)((n + (size_t)TILE - 1) / TILE);
     uint32_t grid = (uint32_t)(di.sm_count * ctas_per_sm[dev]);
     if (grid > tiles) grid = tiles;
-    note_launch_begin(KK_ONESWEEP, stream);
+    if (grid == 0) return RS_OK;
+    note_launch_begin(SEG ? KK_SEG_ONESWEEP : KK_ONESWEEP, stream);
     kern<<<grid, THREADS, L::BYTES, stream>>>(ka, va, kb, vb, n, pass, tiles, ctrl, sticky,
                                               static_cast<S*>(status), static_cast<S*>(status_clear),
-                                              tiles * RADIX, knobs().spin_limit, knobs().debug);
-    note_launch_end(KK_ONESWEEP, stream);
+                                              tiles * RADIX, knobs().spin_limit, knobs().debug,
+                                              seg.tile_geo, seg.gofs);
+    note_launch_end(SEG ? KK_SEG_ONESWEEP : KK_ONESWEEP, stream);
     return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
-template <bool PAIRS, typename S>
+template <bool PAIRS, typename S, bool SEG>
 static rs_status launch_onesweep_typed(int cfg, uint32_t* ka, uint32_t* va, uint32_t* kb,
                                        uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
                                        uint32_t* sticky, void* status, void* status_clear,
-                                       cudaStream_t stream) {
+                                       const SegView& seg, cudaStream_t stream) {
     switch (cfg) {
 #define RS_CASE(I, T, J, B, W)                                                                    \
     case I:                                                                                       \
-        return launch_onesweep_shape<T, J, B, W, PAIRS, S>(ka, va, kb, vb, n, pass, ctrl, sticky, \
-                                                           status, status_clear, stream);
+        return launch_onesweep_shape<T, J, B, W, PAIRS, S, SEG>(ka, va, kb, vb, n, pass, ctrl,    \
+                                                                sticky, status, status_clear,     \
+                                                                seg, stream);
         RS_TILE_SHAPES(RS_CASE)
 #undef RS_CASE
     default: return RS_ERR_INVALID_ARG;

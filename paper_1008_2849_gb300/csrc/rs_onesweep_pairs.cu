@@ -1,4 +1,4 @@
-// rs_onesweep_pairs.cu -- scatter passes of the key-value sort.
+// rs_onesweep_pairs.cu -- scatter passes of the key-value sorts.
 #include "rs_onesweep_launch.cuh"
 
 namespace rs {
@@ -6,12 +6,16 @@ namespace rs {
 rs_status launch_onesweep_pairs(int cfg, bool wide, uint32_t* ka, uint32_t* va, uint32_t* kb,
                                 uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
                                 uint32_t* sticky, void* status, void* status_clear,
-                                cudaStream_t stream) {
+                                const SegView* seg, cudaStream_t stream) {
+    const SegView none{};
+    if (seg != nullptr)  // segment prefixes stay below 2^30: 32-bit status words
+        return launch_onesweep_typed<true, uint32_t, true>(cfg, ka, va, kb, vb, n, pass, ctrl,
+                                                           sticky, status, status_clear, *seg, stream);
     if (wide)
-        return launch_onesweep_typed<true, unsigned long long>(cfg, ka, va, kb, vb, n, pass, ctrl,
-                                                               sticky, status, status_clear, stream);
-    return launch_onesweep_typed<true, uint32_t>(cfg, ka, va, kb, vb, n, pass, ctrl, sticky, status,
-                                                 status_clear, stream);
+        return launch_onesweep_typed<true, unsigned long long, false>(
+            cfg, ka, va, kb, vb, n, pass, ctrl, sticky, status, status_clear, none, stream);
+    return launch_onesweep_typed<true, uint32_t, false>(cfg, ka, va, kb, vb, n, pass, ctrl, sticky,
+                                                        status, status_clear, none, stream);
 }
 
 }  // namespace rs

@@ -1,0 +1,159 @@
+// rs_segmented.cu -- host side of the segmented sort and of the one-CTA sort:
+// workspace layout, launch sequence and the small-sort launcher.
+#include "rs_internal.h"
+#include "rs_segmented.cuh"
+
+namespace rs {
+
+namespace {
+
+// One-CTA sort shapes: 256 threads x 16 items (4096) and 512 x 16 (8192).
+template <int THREADS, int ITEMS, bool PAIRS>
+rs_status launch_small_shape(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                             const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
+                             uint32_t grid, cudaStream_t stream) {
+    constexpr uint32_t CAP = THREADS * ITEMS;
+    constexpr size_t SMEM = ((PAIRS ? 4u : 2u) * CAP + (THREADS / 32) * RADIX) * sizeof(uint32_t);
+    auto kern = k_small_sort<THREADS, ITEMS, PAIRS>;
+    static uint64_t attr_on = 0;  // one bit per device with the attribute set
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
+    if (!((attr_on >> dev) & 1u)) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM) !=
+            cudaSuccess)
+            return RS_ERR_CUDA;
+        attr_on |= 1ull << dev;
+    }
+    note_launch_begin(KK_SMALL, stream);
+    kern<<<grid, THREADS, SMEM, stream>>>(keys, vals, off, small_list, ctrl, single_n);
+    note_launch_end(KK_SMALL, stream);
+    return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+constexpr uint32_t kMinLargeSegment = 4097;  // segments up to 4096 items always take the one-CTA sort
+constexpr int SEG_HIST_THREADS = 512;
+
+}  // namespace
+
+uint32_t small_sort_capacity() { return 8192; }
+
+rs_status launch_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                            const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
+                            uint32_t max_items, cudaStream_t stream) {
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
+    // Single array: one CTA.  Segment list: a grid-stride loop over it.
+    const uint32_t grid = off == nullptr ? 1u : (uint32_t)di.sm_count * 4u;
+    const bool pairs = vals != nullptr;
+    if (max_items <= 4096)
+        return pairs ? launch_small_shape<256, 16, true>(keys, vals, off, small_list, ctrl, single_n,
+                                                         grid, stream)
+                     : launch_small_shape<256, 16, false>(keys, vals, off, small_list, ctrl,
+                                                          single_n, grid, stream);
+    if (max_items <= 8192)
+        return pairs ? launch_small_shape<512, 16, true>(keys, vals, off, small_list, ctrl, single_n,
+                                                         grid, stream)
+                     : launch_small_shape<512, 16, false>(keys, vals, off, small_list, ctrl,
+                                                          single_n, grid, stream);
+    return RS_ERR_INVALID_ARG;
+}
+
+SegLayout seg_layout_for(size_t n, bool pairs, uint32_t num_segments) {
+    SegLayout L{};
+    const size_t tile = (size_t)smallest_tile();
+    const size_t large = std::min<size_t>(num_segments, n / kMinLargeSegment + 1);
+    L.max_large = (uint32_t)large;
+    L.max_tiles = (uint32_t)((n + tile - 1) / tile + large);
+    const size_t status_bytes = (size_t)L.max_tiles * RADIX * 4;
+    size_t off = 0;
+    L.ctrl = off;
+    off = align_up(off + sizeof(Ctrl), 256);
+    L.status0 = off;
+    off = align_up(off + status_bytes, 256);
+    L.status1 = off;
+    off = align_up(off + status_bytes, 256);
+    L.alt_keys = off;
+    off = align_up(off + n * 4, 256);
+    L.alt_vals = off;
+    if (pairs) off = align_up(off + n * 4, 256);
+    L.tile_geo = off;
+    off = align_up(off + (size_t)L.max_tiles * 16, 256);
+    L.small_list = off;
+    off = align_up(off + (size_t)num_segments * 4, 256);
+    L.large_first = off;
+    off = align_up(off + large * 4, 256);
+    L.gofs = off;
+    off = align_up(off + large * PASSES * RADIX * 4, 256);
+    L.total = off;
+    return L;
+}
+
+rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
+                                 const uint32_t* offsets, uint32_t num_segments,
+                                 cudaStream_t stream, void* workspace, size_t workspace_bytes) {
+    const bool pairs = vals != nullptr;
+    const SegLayout L = seg_layout_for(n, pairs, num_segments);
+    if (workspace == nullptr || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
+        return RS_ERR_INVALID_ARG;
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
+    char* ws = static_cast<char*>(workspace);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+    void* status[2] = {ws + L.status0, ws + L.status1};
+    uint32_t* alt_k = reinterpret_cast<uint32_t*>(ws + L.alt_keys);
+    uint32_t* alt_v = pairs ? reinterpret_cast<uint32_t*>(ws + L.alt_vals) : nullptr;
+    uint4* tile_geo = reinterpret_cast<uint4*>(ws + L.tile_geo);
+    uint32_t* small_list = reinterpret_cast<uint32_t*>(ws + L.small_list);
+    uint32_t* large_first = reinterpret_cast<uint32_t*>(ws + L.large_first);
+    uint32_t* gofs = reinterpret_cast<uint32_t*>(ws + L.gofs);
+
+    const int cfg = knobs().tile_config_seg;
+    const uint32_t tile = (uint32_t)(kTileConfigs[cfg].threads * kTileConfigs[cfg].items);
+    uint32_t small_max = (uint32_t)knobs().small_max;
+    if (small_max < kMinLargeSegment - 1) small_max = kMinLargeSegment - 1;
+    if (small_max > small_sort_capacity()) small_max = small_sort_capacity();
+
+    if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return RS_ERR_CUDA;
+    if (L.max_large > 0 &&
+        cudaMemsetAsync(gofs, 0, (size_t)L.max_large * PASSES * RADIX * 4, stream) != cudaSuccess)
+        return RS_ERR_CUDA;
+    note_launch_begin(KK_SEG_PLAN, stream);
+    k_seg_plan<<<1, 1024, 0, stream>>>(offsets, num_segments, n, tile, small_max, ctrl, di.sticky,
+                                       tile_geo, small_list, large_first);
+    note_launch_end(KK_SEG_PLAN, stream);
+    if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
+
+    // Small segments: independent of the large ones (disjoint ranges).
+    st = launch_small_sort(keys, vals, offsets, small_list, ctrl, 0, small_max, stream);
+    if (st != RS_OK) return st;
+
+    // Large segments: histograms, bucket bases, four scatter passes.
+    note_launch_begin(KK_SEG_HIST, stream);
+    k_seg_hist<SEG_HIST_THREADS><<<di.sm_count * 2, SEG_HIST_THREADS, 0, stream>>>(
+        keys, ctrl, tile_geo, gofs, static_cast<uint4*>(status[0]),
+        (uint32_t)((L.status1 - L.status0) / sizeof(uint4)));
+    note_launch_end(KK_SEG_HIST, stream);
+    note_launch_begin(KK_SEG_SCAN, stream);
+    k_seg_scan<<<di.sm_count * 2, 1024, 0, stream>>>(ctrl, gofs, large_first);
+    note_launch_end(KK_SEG_SCAN, stream);
+    if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
+
+    SegView view;
+    view.tile_geo = tile_geo;
+    view.max_tiles = L.max_tiles;
+    for (uint32_t p = 0; p < PASSES; ++p) {
+        view.gofs = gofs;
+        void* cur = status[p & 1];
+        void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;
+        st = pairs ? launch_onesweep_pairs(cfg, false, keys, vals, alt_k, alt_v, n, p, ctrl,
+                                           di.sticky, cur, next, &view, stream)
+                   : launch_onesweep_keys(cfg, false, keys, alt_k, n, p, ctrl, di.sticky, cur, next,
+                                          &view, stream);
+        if (st != RS_OK) return st;
+    }
+    return RS_OK;
+}
+
+}  // namespace rs

@@ -79,6 +79,8 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     DeviceInfo di;
     rs_status st = device_info(&di);
     if (st != RS_OK) return st;
+    if (n <= (uint32_t)knobs().small_max && n <= small_sort_capacity())
+        return launch_small_sort(keys, vals, nullptr, nullptr, nullptr, n, n, stream);
     char* ws = static_cast<char*>(workspace);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
     void* status[2] = {ws + L.status0, ws + L.status1};
@@ -99,9 +101,9 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
         void* cur = status[p & 1];
         void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;
         st = pairs ? launch_onesweep_pairs(cfg, L.wide_status, keys, vals, alt_k, alt_v, n, p, ctrl,
-                                           di.sticky, cur, next, stream)
+                                           di.sticky, cur, next, nullptr, stream)
                    : launch_onesweep_keys(cfg, L.wide_status, keys, alt_k, n, p, ctrl, di.sticky,
-                                          cur, next, stream);
+                                          cur, next, nullptr, stream);
         if (st != RS_OK) return st;
     }
     return RS_OK;

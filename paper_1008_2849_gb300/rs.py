@@ -38,6 +38,10 @@ SIGNATURES = {
     "rs_sort_pairs": (_int, [_vp, _vp, _sz]),
     "rs_sort_keys_ex": (_int, [_vp, _sz, _vp, _vp, _sz]),
     "rs_sort_pairs_ex": (_int, [_vp, _vp, _sz, _vp, _vp, _sz]),
+    "rs_sort_keys_segmented": (_int, [_vp, _sz, _vp, _u32]),
+    "rs_sort_pairs_segmented": (_int, [_vp, _vp, _sz, _vp, _u32]),
+    "rs_sort_keys_segmented_ex": (_int, [_vp, _sz, _vp, _u32, _vp, _vp, _sz]),
+    "rs_sort_pairs_segmented_ex": (_int, [_vp, _vp, _sz, _vp, _u32, _vp, _vp, _sz]),
     "rs_workspace_bytes": (_sz, [_sz, _int, _u32]),
     "rs_stream_status": (_int, [_vp]),
     "rs_status_string": (ctypes.c_char_p, [_int]),
@@ -150,6 +154,46 @@ def sort_pairs_ex(keys, vals, workspace, stream=None) -> None:
            "rs_sort_pairs_ex")
 
 
+def _segments(offsets):
+    n_seg = offsets.numel() - 1
+    if n_seg < 0:
+        raise ValueError("offsets must hold num_segments + 1 entries")
+    return _dev_ptr(offsets, "offsets"), n_seg
+
+
+def sort_keys_segmented(keys, offsets) -> None:
+    """Sort every segment [offsets[s], offsets[s+1]) of a CUDA key tensor in place."""
+    op, ns = _segments(offsets)
+    _check(lib().rs_sort_keys_segmented(_dev_ptr(keys, "keys"), keys.numel(), op, ns),
+           "rs_sort_keys_segmented")
+
+
+def sort_pairs_segmented(keys, vals, offsets) -> None:
+    """Stable sort of every segment of (key, value) pairs, in place."""
+    if vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    op, ns = _segments(offsets)
+    _check(lib().rs_sort_pairs_segmented(_dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"),
+                                         keys.numel(), op, ns), "rs_sort_pairs_segmented")
+
+
+def sort_keys_segmented_ex(keys, offsets, workspace, stream=None) -> None:
+    op, ns = _segments(offsets)
+    _check(lib().rs_sort_keys_segmented_ex(_dev_ptr(keys, "keys"), keys.numel(), op, ns,
+                                           _stream_handle(stream), workspace.data_ptr(),
+                                           workspace.numel()), "rs_sort_keys_segmented_ex")
+
+
+def sort_pairs_segmented_ex(keys, vals, offsets, workspace, stream=None) -> None:
+    if vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    op, ns = _segments(offsets)
+    _check(lib().rs_sort_pairs_segmented_ex(_dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"),
+                                            keys.numel(), op, ns, _stream_handle(stream),
+                                            workspace.data_ptr(), workspace.numel()),
+           "rs_sort_pairs_segmented_ex")
+
+
 def stream_status(stream=None) -> int:
     """Synchronise the stream and return (and clear) the device status code."""
     return int(lib().rs_stream_status(_stream_handle(stream)))
@@ -223,7 +267,8 @@ def profile_read() -> dict:
     return out
 
 
-TUNE_KNOBS = {"tile_pairs": 0, "tile_keys": 1, "hist_ctas_per_sm": 2, "hist_mode": 3}
+TUNE_KNOBS = {"tile_pairs": 0, "tile_keys": 1, "hist_ctas_per_sm": 2, "hist_mode": 3,
+              "small_max": 4, "tile_seg": 5}
 
 
 def tune_set(knob: str, value: int) -> None:
