@@ -134,6 +134,29 @@ rs_status rs_digit_histograms_ex(const uint32_t* d_keys, size_t n, uint32_t* d_h
 rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in,
                              uint32_t* h_keys_out, uint32_t* h_vals_out, size_t n);
 
+/* ---- captured sorts (CUDA graphs) -----------------------------------------
+ * A sort of fixed device buffers captured once into a CUDA graph and then
+ * replayed with one launch: the batched form for serving loops that refill
+ * the same buffers with new data.  Not in the paper. */
+typedef struct rs_graph_s* rs_graph;
+
+/* Capture the sort of d_keys (and d_vals, if not NULL) -- segmented when
+ * num_segments > 0 (d_offsets as for rs_sort_*_segmented), whole otherwise --
+ * with the caller's workspace (>= rs_workspace_bytes(n, d_vals != NULL,
+ * num_segments)) into a new graph, and instantiate it.  Nothing is sorted by
+ * this call; the graph reads the buffers' contents when it is launched.  The
+ * tuning knobs in force now are baked in.  n > 0. */
+rs_status rs_graph_create(rs_graph* out, uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                          const uint32_t* d_offsets, uint32_t num_segments,
+                          void* d_workspace, size_t workspace_bytes);
+
+/* Enqueue one replay of the captured sort on cuda_stream (NULL = legacy
+ * default stream).  Asynchronous; errors via rs_stream_status(). */
+rs_status rs_graph_launch(rs_graph graph, void* cuda_stream);
+
+/* Release the graph.  The buffers and workspace stay the caller's. */
+rs_status rs_graph_destroy(rs_graph graph);
+
 /* ---- sorting without allocating ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory when they sort: code on a
@@ -198,11 +221,27 @@ typedef enum rs_tune_knob {
     RS_TUNE_TILE_SEG = 5          /* tile shape index of the segmented scatter passes */
 } rs_tune_knob;
 
-/* Set a knob; RS_ERR_INVALID_ARG for an unknown knob or out-of-range value. */
+/* Knobs 0, 1, 4 and 5 are kept per size class of the item count -- the
+ * whole array's, or for a segmented sort the average segment's: class 0 up
+ * to 2^13 items, 1 up to 2^16, 2 up to 2^20, 3 up to 2^24, 4 up to 2^28,
+ * 5 above.  Knobs 2 and 3 are global. */
+#define RS_NUM_SIZE_CLASSES 6
+
+/* Set a knob (a per-class knob in every class); RS_ERR_INVALID_ARG for an
+ * unknown knob or out-of-range value. */
 rs_status rs_tune_set(int knob, int value);
 
-/* Current value of a knob, or -1 for an unknown knob. */
+/* Current value of a knob (a per-class knob: its value in class 4), or -1
+ * for an unknown knob. */
 int rs_tune_get(int knob);
+
+/* Set / read a per-class knob in one size class (0 .. RS_NUM_SIZE_CLASSES-1);
+ * -1 / RS_ERR_INVALID_ARG for an unknown class or knob. */
+rs_status rs_tune_set_class(int size_class_index, int knob, int value);
+int rs_tune_get_class(int size_class_index, int knob);
+
+/* Size class of an item count. */
+int rs_size_class(size_t items);
 
 /* Number of tile shapes of the scatter pass compiled into this build. */
 int rs_tile_shape_count(void);

@@ -50,6 +50,7 @@ bool g_prof_on = false;
 std::vector<ProfRec> g_prof_recs;
 std::vector<cudaEvent_t> g_event_pool;
 thread_local cudaEvent_t t_pending_begin = nullptr;
+thread_local bool t_capturing = false;  // inside rs_graph_create: count, but record no events
 
 cudaEvent_t pool_event() {
     if (!g_event_pool.empty()) {
@@ -152,8 +153,22 @@ rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n) 
 }
 
 Knobs& knobs() {
-    static Knobs k{3, 3, kDefaultSpinLimit, 0, 4, 0, 4096, 3};
+    // Defaults chosen by the autotuner on GB300: arrays up to 8192 items take
+    // the one-CTA sort; up to 2^20 items tile shape 1 (512 x 8, two CTAs per
+    // SM); larger ones shape 3 (384 x 12, two CTAs per SM).
+    static Knobs k{{{1, 1, 3, 8192}, {1, 1, 3, 4096}, {1, 1, 3, 4096}, {3, 3, 3, 4096},
+                    {3, 3, 3, 4096}, {3, 3, 3, 4096}},
+                   kDefaultSpinLimit, 0, 4, 0};
     return k;
+}
+
+int size_class(size_t items) {
+    if (items <= (size_t(1) << 13)) return 0;
+    if (items <= (size_t(1) << 16)) return 1;
+    if (items <= (size_t(1) << 20)) return 2;
+    if (items <= (size_t(1) << 24)) return 3;
+    if (items <= (size_t(1) << 28)) return 4;
+    return 5;
 }
 
 const char* kernel_kind_name(int kind) {
@@ -179,7 +194,7 @@ rs_status device_info(DeviceInfo* out) {
 void note_launch_begin(int kind, cudaStream_t stream) {
     (void)kind;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!g_prof_on) return;
+    if (!g_prof_on || t_capturing) return;
     std::lock_guard<std::mutex> lock(g_prof_mu);
     if (!g_prof_on) return;
     t_pending_begin = pool_event();
@@ -383,6 +398,73 @@ rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_i
     return sticky_status(d.s_main);
 }
 
+}  // extern "C"
+
+struct rs_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;  // kernels per replay (for rs_launch_count)
+};
+
+extern "C" {
+
+rs_status rs_graph_create(rs_graph* out, uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                          const uint32_t* d_offsets, uint32_t num_segments, void* d_workspace,
+                          size_t workspace_bytes) {
+    if (out == nullptr || n == 0) return RS_ERR_INVALID_ARG;
+    *out = nullptr;
+    rs_status st = num_segments ? seg_args(d_keys, d_vals, n, d_offsets, num_segments)
+                                : check_sort_args(d_keys, d_vals, n);
+    if (st != RS_OK) return st;
+    const size_t need = num_segments ? seg_layout_for(n, d_vals != nullptr, num_segments).total
+                                     : layout_for(n, d_vals != nullptr).total;
+    if (d_workspace == nullptr || workspace_bytes < need) return RS_ERR_INVALID_ARG;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return RS_ERR_CUDA;
+    rs_graph_s* g = new rs_graph_s();
+    const uint64_t before = g_launches.load(std::memory_order_relaxed);
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(s);
+        delete g;
+        return RS_ERR_CUDA;
+    }
+    t_capturing = true;
+    st = num_segments ? enqueue_sort_segmented(d_keys, d_vals, (uint32_t)n, d_offsets, num_segments,
+                                               s, d_workspace, workspace_bytes)
+                      : enqueue_sort(d_keys, d_vals, (uint32_t)n, s, d_workspace, workspace_bytes);
+    t_capturing = false;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g->graph);
+    g->kernels = g_launches.load(std::memory_order_relaxed) - before;
+    g_launches.fetch_sub(g->kernels, std::memory_order_relaxed);  // captured, not launched
+    cudaStreamDestroy(s);
+    if (st == RS_OK && ce != cudaSuccess) st = RS_ERR_CUDA;
+    if (st == RS_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) st = RS_ERR_CUDA;
+    if (st != RS_OK) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        cudaGetLastError();
+        return st;
+    }
+    *out = g;
+    return RS_OK;
+}
+
+rs_status rs_graph_launch(rs_graph graph, void* cuda_stream) {
+    if (graph == nullptr) return RS_ERR_INVALID_ARG;
+    if (cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess)
+        return RS_ERR_CUDA;
+    g_launches.fetch_add(graph->kernels, std::memory_order_relaxed);
+    return RS_OK;
+}
+
+rs_status rs_graph_destroy(rs_graph graph) {
+    if (graph == nullptr) return RS_ERR_INVALID_ARG;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    delete graph;
+    return RS_OK;
+}
+
 uint64_t rs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 rs_status rs_profile_enable(int on) {
@@ -421,14 +503,35 @@ int rs_profile_read(uint64_t* launches, double* total_ms, int max_kinds) {
 
 const char* rs_kernel_kind_name(int kind) { return kernel_kind_name(kind); }
 
-rs_status rs_tune_set(int knob, int value) {
-    Knobs& k = knobs();
+static rs_status set_class_knob(ClassKnobs& c, int knob, int value) {
     switch (knob) {
     case 0:
     case 1:
+    case 5:
         if (value < 0 || value >= NUM_TILE_CONFIGS) return RS_ERR_INVALID_ARG;
-        (knob == 0 ? k.tile_config_pairs : k.tile_config_keys) = value;
+        (knob == 0 ? c.tile_pairs : knob == 1 ? c.tile_keys : c.tile_seg) = value;
         return RS_OK;
+    case 4:
+        if (value < 0 || value > (int)small_sort_capacity()) return RS_ERR_INVALID_ARG;
+        c.small_max = value;
+        return RS_OK;
+    default: return RS_ERR_INVALID_ARG;
+    }
+}
+
+static int get_class_knob(const ClassKnobs& c, int knob) {
+    switch (knob) {
+    case 0: return c.tile_pairs;
+    case 1: return c.tile_keys;
+    case 4: return c.small_max;
+    case 5: return c.tile_seg;
+    default: return -1;
+    }
+}
+
+rs_status rs_tune_set(int knob, int value) {
+    Knobs& k = knobs();
+    switch (knob) {
     case 2:
         if (value < 1 || value > 16) return RS_ERR_INVALID_ARG;
         k.hist_ctas_per_sm = value;
@@ -437,30 +540,35 @@ rs_status rs_tune_set(int knob, int value) {
         if (value < 0 || value > 2) return RS_ERR_INVALID_ARG;
         k.hist_mode = value;
         return RS_OK;
-    case 4:
-        if (value < 0 || value > (int)small_sort_capacity()) return RS_ERR_INVALID_ARG;
-        k.small_max = value;
+    default:
+        for (int c = 0; c < NUM_SIZE_CLASSES; ++c) {
+            rs_status st = set_class_knob(k.cls[c], knob, value);
+            if (st != RS_OK) return st;
+        }
         return RS_OK;
-    case 5:
-        if (value < 0 || value >= NUM_TILE_CONFIGS) return RS_ERR_INVALID_ARG;
-        k.tile_config_seg = value;
-        return RS_OK;
-    default: return RS_ERR_INVALID_ARG;
     }
 }
 
 int rs_tune_get(int knob) {
     const Knobs& k = knobs();
     switch (knob) {
-    case 0: return k.tile_config_pairs;
-    case 1: return k.tile_config_keys;
     case 2: return k.hist_ctas_per_sm;
     case 3: return k.hist_mode;
-    case 4: return k.small_max;
-    case 5: return k.tile_config_seg;
-    default: return -1;
+    default: return get_class_knob(k.cls[4], knob);
     }
 }
+
+rs_status rs_tune_set_class(int size_class_index, int knob, int value) {
+    if (size_class_index < 0 || size_class_index >= NUM_SIZE_CLASSES) return RS_ERR_INVALID_ARG;
+    return set_class_knob(knobs().cls[size_class_index], knob, value);
+}
+
+int rs_tune_get_class(int size_class_index, int knob) {
+    if (size_class_index < 0 || size_class_index >= NUM_SIZE_CLASSES) return -1;
+    return get_class_knob(knobs().cls[size_class_index], knob);
+}
+
+int rs_size_class(size_t items) { return size_class(items); }
 
 int rs_tile_shape_count(void) { return NUM_TILE_CONFIGS; }
 

@@ -41,16 +41,26 @@ constexpr int NUM_TILE_CONFIGS = 6;
 extern const TileConfig kTileConfigs[NUM_TILE_CONFIGS];
 int smallest_tile();
 
+// Per size class tuning (chosen by the autotuner): tile shapes (indices into
+// kTileConfigs) and the largest array / segment sorted by the one-CTA sort.
+struct ClassKnobs {
+    int tile_pairs;
+    int tile_keys;
+    int tile_seg;
+    int small_max;
+};
+// Size classes by item count (whole array; for a segmented sort the average
+// segment): <= 2^13, <= 2^16, <= 2^20, <= 2^24, <= 2^28, larger.
+constexpr int NUM_SIZE_CLASSES = 6;
+int size_class(size_t items);
+
 // Host-side knobs shared by every launch.
 struct Knobs {
-    int tile_config_pairs;   // index into kTileConfigs
-    int tile_config_keys;
+    ClassKnobs cls[NUM_SIZE_CLASSES];
     uint32_t spin_limit;     // polls per look-back wait before ERR_TIMEOUT
     uint32_t debug;          // DBG_* bits
     int hist_ctas_per_sm;
     int hist_mode;           // HIST_ATOMIC / HIST_LEADER / HIST_MATCH
-    int small_max;           // segments (and whole sorts) up to this size use the one-CTA sort
-    int tile_config_seg;     // tile shape of the segmented scatter passes
 };
 Knobs& knobs();
 

@@ -109,9 +109,10 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
     uint32_t* large_first = reinterpret_cast<uint32_t*>(ws + L.large_first);
     uint32_t* gofs = reinterpret_cast<uint32_t*>(ws + L.gofs);
 
-    const int cfg = knobs().tile_config_seg;
+    const ClassKnobs& ck = knobs().cls[size_class(n / num_segments)];
+    const int cfg = ck.tile_seg;
     const uint32_t tile = (uint32_t)(kTileConfigs[cfg].threads * kTileConfigs[cfg].items);
-    uint32_t small_max = (uint32_t)knobs().small_max;
+    uint32_t small_max = (uint32_t)ck.small_max;
     if (small_max < kMinLargeSegment - 1) small_max = kMinLargeSegment - 1;
     if (small_max > small_sort_capacity()) small_max = small_sort_capacity();
 

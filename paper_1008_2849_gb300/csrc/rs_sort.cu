@@ -79,7 +79,8 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     DeviceInfo di;
     rs_status st = device_info(&di);
     if (st != RS_OK) return st;
-    if (n <= (uint32_t)knobs().small_max && n <= small_sort_capacity())
+    const ClassKnobs& ck = knobs().cls[size_class(n)];
+    if (n <= (uint32_t)ck.small_max && n <= small_sort_capacity())
         return launch_small_sort(keys, vals, nullptr, nullptr, nullptr, n, n, stream);
     char* ws = static_cast<char*>(workspace);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
@@ -96,7 +97,7 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     note_launch_end(KK_PLAN, stream);
     if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
 
-    const int cfg = pairs ? knobs().tile_config_pairs : knobs().tile_config_keys;
+    const int cfg = pairs ? ck.tile_pairs : ck.tile_keys;
     for (uint32_t p = 0; p < PASSES; ++p) {
         void* cur = status[p & 1];
         void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;

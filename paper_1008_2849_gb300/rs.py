@@ -54,6 +54,12 @@ SIGNATURES = {
     "rs_kernel_kind_name": (ctypes.c_char_p, [_int]),
     "rs_tune_set": (_int, [_int, _int]),
     "rs_tune_get": (_int, [_int]),
+    "rs_tune_set_class": (_int, [_int, _int, _int]),
+    "rs_tune_get_class": (_int, [_int, _int]),
+    "rs_size_class": (_int, [_sz]),
+    "rs_graph_create": (_int, [ctypes.POINTER(_vp), _vp, _vp, _sz, _vp, _u32, _vp, _sz]),
+    "rs_graph_launch": (_int, [_vp, _vp]),
+    "rs_graph_destroy": (_int, [_vp]),
     "rs_tile_shape_count": (_int, []),
     "rs_tile_shape": (_int, [_int, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "rs_debug_set_spin_limit": (_int, [_u32]),
@@ -277,6 +283,55 @@ def tune_set(knob: str, value: int) -> None:
 
 def tune_get(knob: str) -> int:
     return int(lib().rs_tune_get(TUNE_KNOBS[knob]))
+
+
+NUM_SIZE_CLASSES = 6
+
+
+def tune_set_class(size_class: int, knob: str, value: int) -> None:
+    _check(lib().rs_tune_set_class(int(size_class), TUNE_KNOBS[knob], int(value)),
+           "rs_tune_set_class(%d, %s)" % (size_class, knob))
+
+
+def tune_get_class(size_class: int, knob: str) -> int:
+    return int(lib().rs_tune_get_class(int(size_class), TUNE_KNOBS[knob]))
+
+
+def size_class(items: int) -> int:
+    return int(lib().rs_size_class(int(items)))
+
+
+class Graph:
+    """A sort of fixed CUDA buffers captured once (rs_graph_create) and
+    replayed with one launch per call (rs_graph_launch)."""
+
+    def __init__(self, keys, vals=None, offsets=None, workspace=None):
+        n = keys.numel()
+        nseg = 0 if offsets is None else offsets.numel() - 1
+        if workspace is None:
+            workspace = alloc_workspace(n, vals is not None, nseg, device=keys.device)
+        self._keep = (keys, vals, offsets, workspace)  # the graph reads these buffers
+        h = _vp()
+        _check(lib().rs_graph_create(ctypes.byref(h), _dev_ptr(keys, "keys"),
+                                     None if vals is None else _dev_ptr(vals, "vals"), n,
+                                     None if offsets is None else _dev_ptr(offsets, "offsets"),
+                                     nseg, workspace.data_ptr(), workspace.numel()),
+               "rs_graph_create")
+        self._h = h
+
+    def launch(self, stream=None) -> None:
+        _check(lib().rs_graph_launch(self._h, _stream_handle(stream)), "rs_graph_launch")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().rs_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tile_shapes():

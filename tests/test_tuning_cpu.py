@@ -1,0 +1,43 @@
+"""CPU-only tests of the per-size-class tuning table (host settings only)."""
+from __future__ import annotations
+
+import json
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def rs():
+    from paper_1008_2849_gb300 import build, rs as _rs
+    build.build_library()
+    _rs.lib()
+    return _rs
+
+
+def test_size_classes(rs):
+    assert rs.size_class(1) == 0 and rs.size_class(8192) == 0
+    assert rs.size_class(8193) == 1 and rs.size_class(1 << 16) == 1
+    assert rs.size_class((1 << 20) + 1) == 3
+    assert rs.size_class(1 << 28) == 4 and rs.size_class((1 << 28) + 1) == 5
+
+
+def test_apply_table_and_restore(rs, tmp_path):
+    from paper_1008_2849_gb300 import autotune
+    saved = {(c, k): rs.tune_get_class(c, k) for c in range(6)
+             for k in ("tile_pairs", "tile_keys", "tile_seg", "small_max")}
+    try:
+        table = {"device": "test", "classes": {"2": {"tile_pairs": 1, "tile_keys": 2},
+                                               "4": {"tile_seg": 5, "small_max": 8192}}}
+        p = tmp_path / "t.json"
+        p.write_text(json.dumps(table))
+        autotune.apply(autotune.load(str(p)))
+        assert rs.tune_get_class(2, "tile_pairs") == 1 and rs.tune_get_class(2, "tile_keys") == 2
+        assert rs.tune_get_class(4, "tile_seg") == 5 and rs.tune_get_class(4, "small_max") == 8192
+        assert rs.tune_get_class(3, "tile_pairs") == saved[(3, "tile_pairs")]
+        with pytest.raises(rs.RsError):
+            rs.tune_set_class(0, "tile_pairs", 99)
+        with pytest.raises(rs.RsError):
+            rs.tune_set_class(7, "tile_pairs", 0)
+    finally:
+        for (c, k), v in saved.items():
+            rs.tune_set_class(c, k, v)
