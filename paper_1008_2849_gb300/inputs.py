@@ -65,6 +65,48 @@ def splitmix32(seed: int, n: int, stream: int = 0, start: int = 0) -> np.ndarray
     return out
 
 
+def _as_i64(x: int) -> int:
+    """The 64-bit two's-complement value of an unsigned 64-bit constant."""
+    x &= 0xFFFFFFFFFFFFFFFF
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def splitmix32_torch(seed: int, n: int, stream: int = 0, start: int = 0, device="cuda", out=None):
+    """The same words as ``splitmix32``, computed with torch int64 arithmetic
+    (wrapping multiplication; right shifts masked to be logical), returned
+    as an int32 tensor holding the uint32 bit patterns.  Used to draw large
+    serving workloads on the device; a CPU test pins it to ``splitmix32``."""
+    import torch
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=device)
+    if n == 0:
+        return out
+    s0 = _as_i64(seed * 256 + stream)
+    g, m1, m2 = _as_i64(0x9E3779B97F4A7C15), _as_i64(0xBF58476D1CE4E5B9), _as_i64(0x94D049BB133111EB)
+    chunk = 1 << 26
+    for c in range(0, n, chunk):
+        m = min(chunk, n - c)
+        z = torch.arange(start + c + 1, start + c + m + 1, dtype=torch.int64, device=out.device)
+        z.mul_(g).add_(s0)
+        z.bitwise_xor_((z >> 30) & ((1 << 34) - 1)).mul_(m1)
+        z.bitwise_xor_((z >> 27) & ((1 << 37) - 1)).mul_(m2)
+        z.bitwise_xor_((z >> 31) & ((1 << 33) - 1))
+        out[c:c + m] = ((z >> 32) & 0xFFFFFFFF).to(torch.int32)
+    return out
+
+
+def keys_torch(dist: str, n: int, seed: int, device="cuda", out=None):
+    """Device-side ``keys`` for the distributions the serving workload uses
+    (``uniform`` and ``and2``); int32 tensor of uint32 bit patterns."""
+    out = splitmix32_torch(seed, n, 0, device=device, out=out)
+    if dist == "uniform":
+        return out
+    if dist == "and2":
+        out.bitwise_and_(splitmix32_torch(seed, n, 1, device=out.device))
+        return out
+    raise ValueError("device-side generator supports uniform and and2, not %r" % dist)
+
+
 def keys(dist: str, n: int, seed: int) -> np.ndarray:
     """``n`` uint32 keys of distribution ``dist`` (see module docstring)."""
     if dist == "uniform":

@@ -1,0 +1,133 @@
+"""Tests of the serving loop.
+
+CPU part: a fake executor sorts with the CPU oracle and completes work after
+a fixed number of polls, so admission, batching and the memory budget can be
+checked without a GPU.  GPU part (marked gpu): the real executor; every
+request's result must equal the oracle's sort of that request alone, however
+requests were batched.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1008_2849_gb300 import inputs
+from paper_1008_2849_gb300.serve import (Request, SerialServer, SortServer, host_keys,
+                                         make_requests)
+
+POOL_N = 1 << 20
+
+
+class FakeExecutor:
+    """Sorts on the host with the oracle; a launch completes after `delay`
+    polls.  Records the bytes it was asked to hold."""
+
+    def __init__(self, delay=3):
+        self.delay = delay
+        self.launched = []
+
+    def bytes_for(self, sizes, with_values, segmented):
+        n = sum(sizes)
+        return n * (8 if with_values else 4) * 2 + 1024
+
+    def launch(self, reqs, segmented):
+        self.launched.append([r.id for r in reqs])
+        out = []
+        for r in reqs:
+            k = host_keys(r, POOL_N)
+            v = inputs.index_values(r.n) if r.with_values else None
+            if segmented:
+                off = np.array([0, r.n], dtype=np.uint32)
+                ko, vo = oracle.sort_pairs_segmented(k, v, off)
+            else:
+                ko, vo = oracle.sort_pairs(k, v)
+            out.append((ko, vo))
+        return {"left": self.delay, "out": out}
+
+    def poll(self, h):
+        h["left"] -= 1
+        return h["left"] <= 0
+
+    def take(self, h, keep):
+        return h["out"] if keep else [(None, None)] * len(h["out"])
+
+    def check(self):
+        pass
+
+
+def _reqs(num, seed, lo=2.0, hi=4.5):
+    return make_requests(num, seed, lo, hi)
+
+
+def test_every_result_is_its_own_sort_cpu():
+    reqs = _reqs(60, 3)
+    ex = FakeExecutor()
+    srv = SortServer(ex, budget_bytes=10**9, max_inflight=4, small_max=2000, batch_items=5000,
+                     keep_results=True)
+    res = srv.run(reqs, realtime=False)
+    assert len(res["done"]) == len(reqs)
+    for d in res["done"]:
+        r = d.request
+        k = host_keys(r, POOL_N)
+        v = inputs.index_values(r.n) if r.with_values else None
+        ko, vo = oracle.sort_pairs(k, v)
+        assert np.array_equal(d.keys, ko)
+        if r.with_values:
+            assert np.array_equal(d.vals, vo)
+    # Small requests were coalesced; batches never mix keys-only with pairs.
+    by_id = {r.id: r for r in reqs}
+    assert any(len(b) > 1 for b in ex.launched)
+    for b in ex.launched:
+        assert len({by_id[i].with_values for i in b}) == 1
+
+
+def test_budget_is_never_exceeded_cpu():
+    reqs = _reqs(80, 4, 2.0, 4.0)
+    ex = FakeExecutor(delay=5)
+    budget = 200_000
+    srv = SortServer(ex, budget_bytes=budget, max_inflight=8, small_max=3000, batch_items=8000)
+    res = srv.run(reqs, realtime=False)
+    assert res["peak_bytes"] <= budget
+    assert len(res["done"]) == len(reqs)
+
+
+def test_oversized_request_is_refused_cpu():
+    reqs = [Request(0, 10_000, True, "uniform", 1)]
+    srv = SortServer(FakeExecutor(), budget_bytes=1000, small_max=100)
+    with pytest.raises(MemoryError):
+        srv.run(reqs, realtime=False)
+
+
+def test_admission_order_cpu():
+    """Requests are admitted in arrival order (a large request at the head
+    is not overtaken by later ones)."""
+    reqs = [Request(0, 50_000, False, "uniform", 1), Request(1, 10, False, "uniform", 2),
+            Request(2, 60_000, True, "and2", 3)]
+    ex = FakeExecutor()
+    SortServer(ex, budget_bytes=10**9, small_max=100).run(reqs, realtime=False)
+    assert [b[0] for b in ex.launched] == [0, 1, 2]
+
+
+@pytest.mark.gpu
+def test_gpu_results_alone_and_in_the_mix():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1008_2849_gb300.serve import GpuExecutor
+    reqs = make_requests(120, 5, 2.0, 5.5)
+    srv = SortServer(GpuExecutor(streams=3, pool_n=POOL_N), budget_bytes=2 * 10**9,
+                     max_inflight=6, small_max=1 << 14, batch_items=1 << 16, keep_results=True)
+    res = srv.run(reqs, realtime=False)
+    assert len(res["done"]) == len(reqs)
+    assert any(d.batch > 1 for d in res["done"])
+    for d in res["done"]:
+        r = d.request
+        k = host_keys(r, POOL_N)
+        v = inputs.index_values(r.n) if r.with_values else None
+        ko, vo = oracle.sort_pairs(k, v)
+        assert np.array_equal(d.keys.cpu().numpy().view(np.uint32), ko), r.id
+        if r.with_values:
+            assert np.array_equal(d.vals.cpu().numpy().view(np.uint32), vo), r.id
+    # The serial baseline sorts the same requests one by one.
+    ser = SerialServer(GpuExecutor(streams=1, pool_n=POOL_N)).run(reqs[:20], realtime=False)
+    assert ser["items_per_s"] > 0

@@ -41,3 +41,20 @@ def test_apply_table_and_restore(rs, tmp_path):
     finally:
         for (c, k), v in saved.items():
             rs.tune_set_class(c, k, v)
+
+
+def test_device_generator_matches_numpy_on_cpu():
+    """The torch generator (used to draw serving workloads on the GPU) gives
+    the same words as the numpy one; checked with torch's CPU backend."""
+    import numpy as np
+    import torch
+
+    from paper_1008_2849_gb300 import inputs
+    for seed, n, start in ((11, 1000, 0), (12345, 70001, 5), (3, 1, 1 << 40)):
+        a = inputs.splitmix32(seed, n, 0, start=start)
+        b = inputs.splitmix32_torch(seed, n, 0, start=start, device="cpu").numpy().view(np.uint32)
+        assert np.array_equal(a, b)
+    for dist in ("uniform", "and2"):
+        a = inputs.keys(dist, 5000, 77)
+        b = inputs.keys_torch(dist, 5000, 77, device="cpu").numpy().view(np.uint32)
+        assert np.array_equal(a, b), dist
