@@ -215,7 +215,8 @@ typedef enum rs_tune_knob {
     RS_TUNE_TILE_PAIRS = 0,       /* tile shape index (rs_tile_shape) of key-value passes */
     RS_TUNE_TILE_KEYS = 1,        /* tile shape index of keys-only passes */
     RS_TUNE_HIST_CTAS_PER_SM = 2, /* CTAs per SM of the histogram kernel, 1..16 */
-    RS_TUNE_HIST_MODE = 3,        /* 0: lane atomics, 1: lane-0 group + atomics, 2: ballot groups */
+    RS_TUNE_HIST_MODE = 3,        /* 0: lane atomics, 1: lane-0 group + atomics, 2: ballot groups,
+                                     3: one private shared column per lane (default) */
     RS_TUNE_SMALL_MAX = 4,        /* arrays and segments up to this size (<= 8192) take the
                                      one-CTA shared-memory sort; segments up to 4096 always do */
     RS_TUNE_TILE_SEG = 5          /* tile shape index of the segmented scatter passes */

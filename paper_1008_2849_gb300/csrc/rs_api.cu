@@ -158,7 +158,7 @@ Knobs& knobs() {
     // SM); larger ones shape 3 (384 x 12, two CTAs per SM).
     static Knobs k{{{1, 1, 3, 8192}, {1, 1, 3, 4096}, {1, 1, 3, 4096}, {3, 3, 3, 4096},
                     {3, 3, 3, 4096}, {3, 3, 3, 4096}},
-                   kDefaultSpinLimit, 0, 4, 0};
+                   kDefaultSpinLimit, 0, 4, 3};
     return k;
 }
 
@@ -537,7 +537,7 @@ rs_status rs_tune_set(int knob, int value) {
         k.hist_ctas_per_sm = value;
         return RS_OK;
     case 3:
-        if (value < 0 || value > 2) return RS_ERR_INVALID_ARG;
+        if (value < 0 || value > 3) return RS_ERR_INVALID_ARG;
         k.hist_mode = value;
         return RS_OK;
     default:

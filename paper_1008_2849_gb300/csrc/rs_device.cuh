@@ -133,6 +133,12 @@ __device__ __forceinline__ void tma_load_1d(void* smem_dst, const void* gmem_src
         ::"r"(smem_u32(smem_dst)), "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
+// Barrier among the first `count` threads of the CTA (count a multiple of
+// 32), on hardware barrier `id` (0 is the one __syncthreads uses).
+__device__ __forceinline__ void named_barrier_sync(uint32_t id, uint32_t count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void record_error(Ctrl* ctrl, uint32_t* sticky, uint32_t bits) {
     atomicOr(&ctrl->err, bits);
     atomicOr(sticky, bits);

@@ -29,6 +29,7 @@ namespace rs {
 constexpr int HIST_ATOMIC = 0;
 constexpr int HIST_LEADER = 1;
 constexpr int HIST_MATCH = 2;
+constexpr int HIST_COLUMNS = 3;  // k_hist4_cols
 
 template <int THREADS, int MODE>
 __global__ void __launch_bounds__(THREADS)
@@ -98,6 +99,63 @@ k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hi
     for (uint32_t i = tid; i < PASSES * RADIX; i += THREADS) {
         const uint32_t c = s_h[i];
         if (c) atomicAdd(hist + i, c);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_hist4_cols: the same histograms with one private column per lane: bin b
+// of digit p, as seen by lane l, lives at word (p*256 + b)*32 + l of a
+// 128 KiB shared array, so the 32 lanes of a warp always add into 32
+// different banks (one shared-memory wavefront per warp-wide add, whatever
+// the keys).  Columns are summed (in rotated order, again conflict-free) at
+// the end.  One CTA per SM.
+// ---------------------------------------------------------------------------
+constexpr uint32_t HIST_COL_WORDS = PASSES * RADIX * 32;
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
+             uint4* __restrict__ clear, uint32_t clear_vec4) {
+    extern __shared__ uint4 s_cols4[];
+    uint32_t* const s_col = reinterpret_cast<uint32_t*>(s_cols4);
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31;
+    for (uint32_t i = tid; i < HIST_COL_WORDS / 4; i += THREADS) s_cols4[i] = make_uint4(0, 0, 0, 0);
+    const uint32_t gtid = blockIdx.x * THREADS + tid;
+    const uint32_t gsize = gridDim.x * THREADS;
+    for (uint32_t i = gtid; i < clear_vec4; i += gsize) clear[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+
+    uint32_t head = (uint32_t)(((16u - ((uintptr_t)keys & 15u)) & 15u) >> 2);
+    if (head > n) head = n;
+    const uint32_t body4 = (n - head) >> 2;
+    const uint32_t tail = head + body4 * 4;
+    const uint4* __restrict__ body = reinterpret_cast<const uint4*>(keys + head);
+    uint32_t* const mycol = s_col + lane;
+    auto count_key = [&](uint32_t key) {
+#pragma unroll
+        for (uint32_t p = 0; p < PASSES; ++p)
+            atomicAdd(mycol + ((p * RADIX + ((key >> (p * RADIX_BITS)) & (RADIX - 1))) << 5), 1u);
+    };
+    // Two independent 16-byte loads in flight per thread and iteration.
+    for (uint32_t i = gtid; i < body4; i += 2 * gsize) {
+        const uint4 v0 = ld_stream(body + i);
+        const bool has1 = i + gsize < body4;
+        const uint4 v1 = has1 ? ld_stream(body + i + gsize) : make_uint4(0, 0, 0, 0);
+        count_key(v0.x); count_key(v0.y); count_key(v0.z); count_key(v0.w);
+        if (has1) { count_key(v1.x); count_key(v1.y); count_key(v1.z); count_key(v1.w); }
+    }
+    if (blockIdx.x == 0 && tid < 8) {
+        const uint32_t i = tid < 4 ? tid : tail + (tid - 4);
+        const bool ok = tid < 4 ? i < head : i < n;
+        if (ok) count_key(keys[i]);
+    }
+    __syncthreads();
+    for (uint32_t bin = tid; bin < PASSES * RADIX; bin += THREADS) {
+        uint32_t c = 0;
+#pragma unroll 8
+        for (uint32_t j = 0; j < 32; ++j) c += s_col[(bin << 5) + ((j + bin) & 31)];
+        if (c) atomicAdd(hist + bin, c);
     }
 }
 

@@ -114,6 +114,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     __shared__ uint32_t s_gbase[RADIX];  // G[pass][b]
     __shared__ uint32_t s_gofs[RADIX];   // G + before_tile - tile_excl, per tile
     __shared__ uint32_t s_cnt[RADIX];    // digit counts of the next tile to rank
+    __shared__ uint32_t s_excl[RADIX];   // their exclusive prefix over digits
     __shared__ uint32_t s_scan[RADIX / 32];
     __shared__ uint32_t s_ids[4];
     __shared__ uint4 s_geo[4];  // segmented: geometry of the tiles in s_ids
@@ -219,18 +220,39 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 if (j * 32 + lane < left) atomicAdd(&row[(keys[j * 32] >> shift) & (RADIX - 1)], 1u);
         }
     };
-    // Publish the counts of tile t (per-warp counts in wcnt): AGG, or INC for
-    // tile 0.
-    auto publish_counts = [&](uint32_t t, uint32_t first) {
-        if (tid < RADIX) {
-            uint32_t c = 0;
+    // Threads < 256 only, once the per-warp counts of tile t are in wcnt:
+    // publish the tile's counts (AGG, or INC for the first tile of its
+    // segment), keep them and their exclusive prefix over digits for the
+    // look-back, and turn wcnt into every warp's first tile position of every
+    // digit.  The 256 threads synchronise among themselves (named barrier 1).
+    auto prep_tile = [&](uint32_t t, uint32_t first) {
+        uint32_t c = 0;
 #pragma unroll
-            for (uint32_t w = 0; w < WARPS; ++w) c += s_wcnt[w * RADIX + tid];
-            s_cnt[tid] = c;  // the tile's counts, reused when the tile is ranked
-            const bool withhold = (debug & DBG_WITHHOLD_FIRST_TILE) && t == 0;
-            if (!withhold)
-                st_relaxed(status + (size_t)t * RADIX + tid, (t == first ? SW::INC : SW::AGG) | (S)c);
+        for (uint32_t w = 0; w < WARPS; ++w) c += s_wcnt[w * RADIX + tid];
+        s_cnt[tid] = c;
+        const bool withhold = (debug & DBG_WITHHOLD_FIRST_TILE) && t == 0;
+        if (!withhold)
+            st_relaxed(status + (size_t)t * RADIX + tid, (t == first ? SW::INC : SW::AGG) | (S)c);
+        uint32_t x = c;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
+        if (lane == 31) s_scan[warp] = x;
+        named_barrier_sync(1, RADIX);
+        uint32_t off = 0;
+        for (uint32_t w = 0; w < warp; ++w) off += s_scan[w];
+        const uint32_t excl = off + x - c;
+        s_excl[tid] = excl;
+        uint32_t run = excl;
+#pragma unroll
+        for (uint32_t w = 0; w < WARPS; ++w) {
+            const uint32_t v = s_wcnt[w * RADIX + tid];
+            s_wcnt[w * RADIX + tid] = run;
+            run += v;
+        }
+        named_barrier_sync(1, RADIX);  // s_scan may be rewritten for the next tile
     };
 
     // Prologue: the first tile's data and counts; the second tile's id is taken
@@ -241,7 +263,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     wait_bar(0);
     count_slots_of(0, s_geo[0].y, warp);
     __syncthreads();
-    publish_counts(s_ids[0], s_geo[0].z);
+    if (tid < RADIX) prep_tile(s_ids[0], s_geo[0].z);
     if (tid == 0) {
         s_ids[1] = atomicAdd(&ctrl->tile_ctr[pass], 1u);
         s_geo[1] = load_geo(s_ids[1]);
@@ -270,31 +292,6 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         const uint32_t valid = geo.y;
         const uint32_t first_tile = geo.z;  // look-back stops here
         uint32_t* const in_k = smem + L::IN_K + buf * TILE;
-
-        // ---- 1. counts, prefix over digits, per-warp positions -----------
-        const uint32_t count = tid < RADIX ? s_cnt[tid] : 0u;
-        uint32_t x = count;
-#pragma unroll
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (tid < RADIX && lane == 31) s_scan[warp] = x;
-        __syncthreads();
-        uint32_t excl_in_tile = 0;
-        if (tid < RADIX) {
-            uint32_t off = 0;
-            for (uint32_t w = 0; w < warp; ++w) off += s_scan[w];
-            excl_in_tile = off + x - count;
-            uint32_t run = excl_in_tile;
-#pragma unroll
-            for (uint32_t w = 0; w < WARPS; ++w) {
-                const uint32_t c = s_wcnt[w * RADIX + tid];
-                s_wcnt[w * RADIX + tid] = run;
-                run += c;
-            }
-        }
-        __syncthreads();
 
         // ---- 2. rank, and stage the keys ------------------------------------
         uint32_t* const cnt = s_wcnt + warp * RADIX;
@@ -339,10 +336,11 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             reinterpret_cast<uint4*>(cnt)[i] = make_uint4(0, 0, 0, 0);
         __syncthreads();
 
-        // ---- 3. look-back (threads < 256) || count the next tile ------------
+        // ---- 3. look-back (threads < 256) || count the next tile; values ----
         uint32_t next_id = 0;
         uint4 next_geo = make_uint4(0, 0, 0, 0);
         if (tid < RADIX) {
+            const uint32_t count = s_cnt[tid];
             S before_tile = 0;
             if (tile > first_tile) {
                 int32_t t = (int32_t)tile - 1;
@@ -384,7 +382,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 st_relaxed(status + (size_t)tile * RADIX + tid,
                            SW::INC | ((before_tile + (S)count) & SW::VALUE));
             }
-            s_gofs[tid] = (SEG ? seg_base : s_gbase[tid]) + (uint32_t)before_tile - excl_in_tile;
+            s_gofs[tid] = (SEG ? seg_base : s_gbase[tid]) + (uint32_t)before_tile - s_excl[tid];
             if (tid == 0) {
                 if (s_err_seen) s_flag = 1;
                 // This CTA waits on no other CTA from here until the counts of
@@ -409,16 +407,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 count_slots_of(buf ^ 1, nvalid, warp);
             }
         }
-        __syncthreads();
-        if (have_next) publish_counts(nxt, ngeo.z);
-        if (s_flag) {
-            // An error somewhere: write nothing more.  The next tile's keys
-            // have landed; let this tile's values land too before exiting.
-            if (PAIRS) wait_bar(2);
-            break;
-        }
-
-        // ---- 4. stage the values, then fetch the next tile's ----------------
+        // Every thread stages its own items' values (the key buffer is free).
         if (PAIRS) {
             wait_bar(2);
             uint32_t vv[ITEMS];
@@ -432,11 +421,13 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 for (int j = 0; j < ITEMS; ++j)
                     if (wofs + j * 32 + lane < valid) in_k[pos[j]] = vv[j];
             }
-            __syncthreads();
-            if (have_next) issue_copy(smem + L::IN_V, src_v, ngeo, &s_bar[2]);
         }
+        __syncthreads();
+        if (s_flag) break;  // an error somewhere: write nothing more (no copy is in flight)
+        if (PAIRS && have_next) issue_copy(smem + L::IN_V, src_v, ngeo, &s_bar[2]);
 
-        // ---- 5. coalesced stores of the bucket runs -------------------------
+        // ---- 4. the next tile's counts, prefix and bases || this tile's stores
+        if (have_next && tid < RADIX) prep_tile(nxt, ngeo.z);
         bool bad = false;
         auto scatter_tile = [&](auto full) {
             constexpr bool FULL = decltype(full)::value;

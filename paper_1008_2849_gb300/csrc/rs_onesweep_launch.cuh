@@ -14,7 +14,7 @@ namespace rs {
     X(1, 512, 8, 2, 16)     \
     X(2, 256, 16, 2, 32)    \
     X(3, 384, 12, 2, 16)    \
-    X(4, 768, 8, 1, 32)     \
+    X(4, 384, 12, 2, 32)    \
     X(5, 1024, 8, 1, 32)
 
 template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S, bool SEG>

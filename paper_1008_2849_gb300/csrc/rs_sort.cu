@@ -7,7 +7,7 @@ namespace rs {
 
 // Must list the shapes of RS_TILE_SHAPES (rs_onesweep_launch.cuh) in order.
 const TileConfig kTileConfigs[NUM_TILE_CONFIGS] = {{512, 16, 1}, {512, 8, 2}, {256, 16, 2},
-                                                   {384, 12, 2}, {768, 8, 1}, {1024, 8, 1}};
+                                                   {384, 12, 2}, {384, 12, 2}, {1024, 8, 1}};
 
 int smallest_tile() {
     int t = kTileConfigs[0].threads * kTileConfigs[0].items;
@@ -50,6 +50,27 @@ static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, v
     const uint32_t needed = (vec4 + 63) / 64 / (HIST_THREADS / 32) + 1;  // 64 vectors per warp
     if (blocks > needed) blocks = needed;
     if (blocks < 1) blocks = 1;
+    if (knobs().hist_mode == HIST_COLUMNS) {
+        constexpr int T = 1024;
+        constexpr size_t SMEM = HIST_COL_WORDS * sizeof(uint32_t);
+        static uint64_t attr_on = 0;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
+        if (!((attr_on >> dev) & 1u)) {
+            if (cudaFuncSetAttribute(k_hist4_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM) != cudaSuccess)
+                return RS_ERR_CUDA;
+            attr_on |= 1ull << dev;
+        }
+        uint32_t grid = (uint32_t)di.sm_count;
+        const uint32_t need = (vec4 + T - 1) / T;
+        if (grid > need) grid = need > 0 ? need : 1;
+        note_launch_begin(KK_HIST, stream);
+        k_hist4_cols<T><<<grid, T, SMEM, stream>>>(keys, n, hist, static_cast<uint4*>(clear),
+                                                    (uint32_t)(clear_bytes / sizeof(uint4)));
+        note_launch_end(KK_HIST, stream);
+        return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+    }
     auto kern = k_hist4<HIST_THREADS, HIST_LEADER>;
     switch (knobs().hist_mode) {
     case HIST_ATOMIC: kern = k_hist4<HIST_THREADS, HIST_ATOMIC>; break;
