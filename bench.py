@@ -58,6 +58,28 @@ def dist_env():
     return world, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """Key seed of rank `rank`'s array: every replica sorts its own input."""
+    return KEY_SEED + 1000 * rank
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The maximum of `x` over all ranks (the slowest replica sets the job's
+    time); `x` itself on a single rank, where no process group exists."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, n: int, seconds: float) -> float:
+    """Items per second for the whole job: all ranks' items over the time."""
+    return world * steps * n / seconds
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -119,7 +141,7 @@ def run_reference(args, world, rank):
     import oracle
     oracle.build()
     threads = os.cpu_count() or 1
-    n_sample = 1 << 24
+    n_sample = 1 << args.reference_sample_log2
     k = inputs.keys("uniform", n_sample, seed=KEY_SEED)
     v = inputs.index_values(n_sample)
     for _ in range(args.warmup):
@@ -137,8 +159,8 @@ def run_reference(args, world, rank):
         "config": {"workload": WORKLOAD, "n": N_PAIRS, "key_dist": "uniform", "seed": KEY_SEED,
                    "values": "index", "reference_sample_n": n_sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "each step sorts 2^24 of the workload's pairs on the host "
-                                   "(threaded LSD counting-sort oracle)"},
+                         "sample": "each step sorts 2^%d of the workload's pairs on the host "
+                                   "(threaded LSD counting-sort oracle)" % args.reference_sample_log2},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -153,6 +175,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-sample-log2", type=int, default=24,
+                    help="--impl reference: log2 of the pairs each step sorts on the host")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3  # at least three untimed warm-up steps
@@ -173,7 +197,7 @@ def main():
     rs.lib()
 
     n = N_PAIRS
-    seed = KEY_SEED + 1000 * rank  # every rank sorts an independent array
+    seed = replica_seed(rank)
     k_host = inputs.keys("uniform", n, seed=seed)
     v_host = inputs.index_values(n)
     dev = torch.device("cuda", local)
@@ -217,11 +241,8 @@ def main():
     rs.check_stream(stream)
     elapsed_ms = ev0.elapsed_time(ev1)
 
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
-    value = world * args.steps * n / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, world, dev)
+    value = job_throughput(world, args.steps, n, elapsed_ms / 1e3)
 
     # Roofline of the dominant kernel: the scatter pass.
     peaks, peak_src = measured_peaks()
@@ -260,12 +281,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             rs.sort_pairs_host(kin, vin, kout, vout)
-        dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-        e2e = {"value": world * e2e_steps * n / dt, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_throughput(world, e2e_steps, n, dt), "unit": UNIT,
                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                "api": "rs_sort_pairs_host (pinned host buffers)", "steps": e2e_steps}
 
