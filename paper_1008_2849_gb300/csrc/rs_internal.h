@@ -31,13 +31,27 @@ const char* kernel_kind_name(int kind);
 void note_launch_begin(int kind, cudaStream_t stream);
 void note_launch_end(int kind, cudaStream_t stream);
 
-// Tile shapes of the scatter kernel that this build instantiates.
+// Tile shapes of the scatter kernel that this build instantiates:
+// X(index, threads, items per thread, CTAs per SM the register budget is
+// sized for, look-back window in status words).  The launchers and the host
+// tables are both generated from this one list.
+#define RS_TILE_SHAPES(X)   \
+    X(0, 512, 16, 1, 32)    \
+    X(1, 512, 8, 2, 16)     \
+    X(2, 256, 16, 2, 32)    \
+    X(3, 384, 12, 2, 8)     \
+    X(4, 384, 12, 2, 16)    \
+    X(5, 1024, 8, 1, 32)
+
 struct TileConfig {
     int threads;
     int items;
     int min_blocks;  // CTAs per SM the register budget is sized for
+    int window;      // look-back window (status words read per round trip)
 };
-constexpr int NUM_TILE_CONFIGS = 6;
+#define RS_COUNT_SHAPE(I, T, J, B, W) +1
+constexpr int NUM_TILE_CONFIGS = 0 RS_TILE_SHAPES(RS_COUNT_SHAPE);
+#undef RS_COUNT_SHAPE
 extern const TileConfig kTileConfigs[NUM_TILE_CONFIGS];
 int smallest_tile();
 

@@ -97,6 +97,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
     using SW = StatusWord<S>;
     static_assert(THREADS >= (int)RADIX && THREADS % 32 == 0, "one thread per digit");
+    static_assert(RADIX_BITS == 8, "digits are whole bytes of the key");
     constexpr uint32_t WARPS = L::WARPS;
     constexpr uint32_t TILE = L::TILE;
     constexpr uint32_t WARP_ITEMS = 32 * ITEMS;
@@ -104,6 +105,13 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     constexpr uint32_t LB_WARPS = RADIX / 32;                   // warps of the look-back
     constexpr bool SPARE = WARPS > LB_WARPS;                    // warps free to count meanwhile
     constexpr uint32_t ISSUER = THREADS - 1;                    // issues the bulk copies
+    // Store split of the staged tile (see the scatter below): threads >= RADIX
+    // do no prep of the next tile, so they take a larger share of the stores.
+    constexpr uint32_t FREE = THREADS - RADIX;
+    constexpr uint32_t EARLY_PER =
+        FREE == 0 ? 0 : ((ITEMS * 3) / 2 < (TILE / 2) / FREE ? (ITEMS * 3) / 2 : (TILE / 2) / FREE);
+    constexpr uint32_t EARLY = EARLY_PER * FREE;
+    constexpr uint32_t LATE_PER = (TILE - EARLY + THREADS - 1) / THREADS;
     static_assert(L::BYTES + 4096 <= 232448, "shared memory plan exceeds one CTA's limit");
 
     extern __shared__ uint4 s_dyn[];
@@ -203,7 +211,10 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         }
         phase ^= 1u << b;
     };
-    const uint32_t shift = pass * RADIX_BITS;
+    // Digit of a key: byte `pass`, picked by one byte permute (the other
+    // three result bytes come from the zero operand).
+    const uint32_t dsel = 0x4440u | pass;
+    auto digit_of = [dsel](uint32_t key) { return __byte_perm(key, 0u, dsel); };
     const uint32_t wofs = warp * WARP_ITEMS;
     // Count the slots of warp w of the tile in key buffer b into wcnt row w.
     auto count_slots_of = [&](uint32_t b, uint32_t valid, uint32_t w) {
@@ -212,12 +223,12 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         if (valid == TILE) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)
-                atomicAdd(&row[(keys[j * 32] >> shift) & (RADIX - 1)], 1u);
+                atomicAdd(&row[digit_of(keys[j * 32])], 1u);
         } else {
             const uint32_t left = valid > w * WARP_ITEMS ? valid - w * WARP_ITEMS : 0u;
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)
-                if (j * 32 + lane < left) atomicAdd(&row[(keys[j * 32] >> shift) & (RADIX - 1)], 1u);
+                if (j * 32 + lane < left) atomicAdd(&row[digit_of(keys[j * 32])], 1u);
         }
     };
     // Threads < 256 only, once the per-warp counts of tile t are in wcnt:
@@ -226,9 +237,16 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     // look-back, and turn wcnt into every warp's first tile position of every
     // digit.  The 256 threads synchronise among themselves (named barrier 1).
     auto prep_tile = [&](uint32_t t, uint32_t first) {
+        // Up to 16 warps the counts stay in registers for the rewrite below.
+        constexpr uint32_t KEPT = WARPS <= 16 ? WARPS : 1;
+        uint32_t kept[KEPT];
         uint32_t c = 0;
 #pragma unroll
-        for (uint32_t w = 0; w < WARPS; ++w) c += s_wcnt[w * RADIX + tid];
+        for (uint32_t w = 0; w < WARPS; ++w) {
+            const uint32_t v = s_wcnt[w * RADIX + tid];
+            if (WARPS <= 16) kept[w < KEPT ? w : 0] = v;
+            c += v;
+        }
         s_cnt[tid] = c;
         const bool withhold = (debug & DBG_WITHHOLD_FIRST_TILE) && t == 0;
         if (!withhold)
@@ -248,7 +266,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         uint32_t run = excl;
 #pragma unroll
         for (uint32_t w = 0; w < WARPS; ++w) {
-            const uint32_t v = s_wcnt[w * RADIX + tid];
+            const uint32_t v = WARPS <= 16 ? kept[w < KEPT ? w : 0] : s_wcnt[w * RADIX + tid];
             s_wcnt[w * RADIX + tid] = run;
             run += v;
         }
@@ -306,7 +324,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 const bool is_live = FULL || j * 32 + lane < left;
                 const uint32_t live = FULL ? 0xffffffffu : prefix_lanes(j * 32, left);
                 const uint32_t k = keys[j * 32];
-                const uint32_t d = (k >> shift) & (RADIX - 1);
+                const uint32_t d = digit_of(k);
                 uint32_t peers;
                 if (j & 1) {
                     peers = match_label<RADIX_BITS>(d) & live;  // integer pipe
@@ -347,27 +365,42 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 const int32_t lo = (int32_t)first_tile;
                 uint32_t spins = 0;
                 while (true) {
+                    // Status words of tiles t, t-1, ..., t-WIN+1 (INC 0 before lo).
                     S lb[WIN];
+                    const S* at = status + (size_t)t * RADIX + tid;
+                    if (t - (WIN - 1) >= lo) {  // CTA-uniform
 #pragma unroll
-                    for (int i = 0; i < WIN; ++i)
-                        lb[i] = (t - i >= lo) ? ld_relaxed(status + (size_t)(t - i) * RADIX + tid)
-                                              : SW::INC;
-                    int used = 0;
-                    bool done = false;
+                        for (int i = 0; i < WIN; ++i) lb[i] = ld_relaxed(at - (size_t)i * RADIX);
+                    } else {
 #pragma unroll
-                    for (int i = 0; i < WIN; ++i) {
-                        const S flag = lb[i] & SW::FLAGS;
-                        if (flag == 0) break;  // not published yet: wait for this one
-                        before_tile += lb[i] & SW::VALUE;
-                        used = i + 1;
-                        if (flag == SW::INC) {
-                            done = true;
-                            break;
+                        for (int i = 0; i < WIN; ++i)
+                            lb[i] = (t - i >= lo) ? ld_relaxed(at - (size_t)i * RADIX) : SW::INC;
+                    }
+                    // The walk adds the AGG words, nearest first, up to the first
+                    // other word: an INC (added; the walk is done) or a word not
+                    // published yet (waited for).  stop = its index, WIN if none.
+                    int stop = WIN;
+                    S end = 0;
+#pragma unroll
+                    for (int i = WIN - 1; i >= 0; --i) {
+                        if ((lb[i] & SW::FLAGS) != SW::AGG) {
+                            stop = i;
+                            end = lb[i];
                         }
                     }
-                    if (done) break;
-                    t -= used;
-                    if (used == WIN) continue;
+                    // Words before `stop` all carry the AGG flag: add them whole and
+                    // take the flags off at once (wrap-around arithmetic).
+                    S sum = 0;
+#pragma unroll
+                    for (int i = 0; i < WIN; ++i)
+                        if (i < stop) sum += lb[i];
+                    before_tile += sum - (S)stop * SW::AGG;
+                    if ((end & SW::FLAGS) == SW::INC) {
+                        before_tile += end & SW::VALUE;
+                        break;
+                    }
+                    t -= stop;
+                    if (stop == WIN) continue;
                     if (++spins > spin_limit) {
                         record_error(ctrl, sticky, ERR_TIMEOUT);
                         __threadfence();  // error visible before the INC below
@@ -428,15 +461,16 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
 
         // ---- 4. the next tile's counts, prefix and bases || this tile's stores
         if (have_next && tid < RADIX) prep_tile(nxt, ngeo.z);
+        // Staged slots [0, EARLY) are stored by the threads that do no prep,
+        // which start at once; slots [EARLY, TILE) by every thread, the prep
+        // threads joining once the next tile's prep is done.
         bool bad = false;
         auto scatter_tile = [&](auto full) {
             constexpr bool FULL = decltype(full)::value;
-#pragma unroll
-            for (int k = 0; k < ITEMS; ++k) {
-                const uint32_t s = k * THREADS + tid;
+            auto store_slot = [&](uint32_t s) {
                 if (FULL || s < valid) {
                     const uint32_t kk = s_stage[s];
-                    const uint32_t g = s_gofs[(kk >> shift) & (RADIX - 1)] + s;
+                    const uint32_t g = s_gofs[digit_of(kk)] + s;
                     if (g < n) {
                         dst_k[g] = kk;
                         if (PAIRS) dst_v[g] = in_k[s];
@@ -444,6 +478,15 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                         bad = true;
                     }
                 }
+            };
+            if (FREE > 0 && tid >= RADIX) {
+#pragma unroll
+                for (uint32_t k = 0; k < EARLY_PER; ++k) store_slot(k * FREE + (tid - RADIX));
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < LATE_PER; ++k) {
+                const uint32_t s = EARLY + k * THREADS + tid;
+                if ((TILE - EARLY) % THREADS == 0 || s < TILE) store_slot(s);
             }
         };
         if (valid == TILE)

@@ -7,16 +7,6 @@
 
 namespace rs {
 
-// The tile shapes of kTileConfigs (rs_sort.cu), in the same order:
-// (index, threads, items per thread, CTAs per SM, look-back window).
-#define RS_TILE_SHAPES(X)   \
-    X(0, 512, 16, 1, 32)    \
-    X(1, 512, 8, 2, 16)     \
-    X(2, 256, 16, 2, 32)    \
-    X(3, 384, 12, 2, 16)    \
-    X(4, 384, 12, 2, 32)    \
-    X(5, 1024, 8, 1, 32)
-
 template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S, bool SEG>
 static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
                                        uint32_t n, uint32_t pass, Ctrl* ctrl, uint32_t* sticky,

@@ -6,8 +6,9 @@
 namespace rs {
 
 // Must list the shapes of RS_TILE_SHAPES (rs_onesweep_launch.cuh) in order.
-const TileConfig kTileConfigs[NUM_TILE_CONFIGS] = {{512, 16, 1}, {512, 8, 2}, {256, 16, 2},
-                                                   {384, 12, 2}, {384, 12, 2}, {1024, 8, 1}};
+#define RS_SHAPE_ENTRY(I, T, J, B, W) {T, J, B, W},
+const TileConfig kTileConfigs[NUM_TILE_CONFIGS] = {RS_TILE_SHAPES(RS_SHAPE_ENTRY)};
+#undef RS_SHAPE_ENTRY
 
 int smallest_tile() {
     int t = kTileConfigs[0].threads * kTileConfigs[0].items;
