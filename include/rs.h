@@ -88,9 +88,11 @@ rs_status rs_sort_pairs_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n,
  * d_offsets[num_segments]) are left as they are; a single segment must hold
  * fewer than 2^30 items.  A table that breaks these rules is detected on the
  * device: nothing is written and the status is RS_ERR_BAD_SEGMENTS.
- * Segments of at most 4096 items (or the RS_TUNE_SMALL_MAX setting, up to
- * 8192) are sorted by one CTA each in shared memory; larger ones by the
- * four scatter passes of the unsegmented sort, all large segments together.
+ * Segments of at most 512 items (the RS_TUNE_WARP_MAX setting) are sorted
+ * by one warp each, segments of at most 4096 items (or the RS_TUNE_SMALL_MAX
+ * setting, up to 8192) by one CTA each, both in shared memory; larger ones by
+ * the four scatter passes of the unsegmented sort, all large segments
+ * together.
  * Plain forms are synchronous; _ex forms as above, with
  * workspace_bytes >= rs_workspace_bytes(n, with_values, num_segments). */
 rs_status rs_sort_keys_segmented(uint32_t* d_keys, size_t n, const uint32_t* d_offsets,
@@ -219,10 +221,14 @@ typedef enum rs_tune_knob {
                                      3: one private shared column per lane (default) */
     RS_TUNE_SMALL_MAX = 4,        /* arrays and segments up to this size (<= 8192) take the
                                      one-CTA shared-memory sort; segments up to 4096 always do */
-    RS_TUNE_TILE_SEG = 5          /* tile shape index of the segmented scatter passes */
+    RS_TUNE_TILE_SEG = 5,         /* tile shape index of the segmented scatter passes */
+    RS_TUNE_WARP_MAX = 6,         /* arrays and segments up to this size (<= 512) take the
+                                     one-warp shared-memory sort; 0 or 1 turns it off */
+    RS_TUNE_SMALL_BITS = 7        /* digit width of the one-warp and one-CTA sorts: 8 (four
+                                     passes, the default) or 4 (eight passes) */
 } rs_tune_knob;
 
-/* Knobs 0, 1, 4 and 5 are kept per size class of the item count -- the
+/* Knobs 0, 1 and 4..7 are kept per size class of the item count -- the
  * whole array's, or for a segmented sort the average segment's: class 0 up
  * to 2^13 items, 1 up to 2^16, 2 up to 2^20, 3 up to 2^24, 4 up to 2^28,
  * 5 above.  Knobs 2 and 3 are global. */

@@ -6,14 +6,15 @@ captured CUDA graphs (rs_graph_*) of a representative synthetic workload
 under every candidate setting and keeps the fastest:
 
 * whole arrays: the tile shape of the scatter passes, for key-value and for
-  keys-only sorts, and whether arrays up to 8192 items take the one-CTA
-  shared-memory sort;
+  keys-only sorts; for arrays up to 8192 items, which take the one-warp sort
+  (up to 512 items) and the one-CTA sort, and at which digit width;
 * segmented batches: the tile shape of the segmented scatter passes and the
-  largest segment sorted by the one-CTA sort (4096 or 8192).
+  largest segment sorted by the one-CTA sort (4096 or 8192); for batches of
+  short arrays the largest segment sorted by the one-warp sort and the digit
+  width of the on-chip sorts (4 bits, eight passes, or 8 bits, four passes).
 
-The digit width is not a candidate: this build's passes are fixed at 8-bit
-digits (four passes over 32-bit keys).  Results never depend on the
-settings, only speed does.  The table is JSON:
+The scatter passes of large arrays keep 8-bit digits (four passes over
+32-bit keys).  Results never depend on the settings, only speed does.  The table is JSON:
 
     {"device": "...", "classes": {"3": {"tile_pairs": 3, "tile_keys": 3, ...}}}
 
@@ -83,25 +84,69 @@ def tune_whole(rs, torch, inputs, reps=3, quick=False):
 
 
 def tune_one_cta(rs, torch, inputs, reps=3):
-    """Class 0 (up to 2^13 items): one-CTA sort (threshold 8192) or the
-    scatter passes (threshold 4096), timed at 8192 pairs."""
-    n = 1 << 13
-    k = torch.from_numpy(inputs.keys("uniform", n, seed=300).view(np.int32)).cuda()
-    v = torch.arange(n, dtype=torch.int32, device="cuda")
-    kb, vb = torch.empty_like(k), torch.empty_like(v)
-    old = rs.tune_get_class(0, "small_max")
+    """Class 0 (up to 2^13 items): which arrays take the one-warp sort
+    (warp_max 0 or 512) and the one-CTA sort (small_max 4096 or 8192), and the
+    digit width of both (4 or 8 bits), timed at 512 and at 8192 pairs; the
+    score of a setting is the sum of its two times over the best ones."""
+    cases = {}
+    for n in (512, 8192):
+        k = torch.from_numpy(inputs.keys("uniform", n, seed=300).view(np.int32)).cuda()
+        v = torch.arange(n, dtype=torch.int32, device="cuda")
+        cases[n] = (k, v, torch.empty_like(k), torch.empty_like(v))
+    names = ("warp_max", "small_max", "small_bits")
+    old = {k: rs.tune_get_class(0, k) for k in names}
     res = {}
-    for small in (4096, 8192):
-        rs.tune_set_class(0, "small_max", small)
+    for warp_max in (0, 512):
+        for small in (4096, 8192):
+            for bits in (4, 8):
+                for name, val in zip(names, (warp_max, small, bits)):
+                    rs.tune_set_class(0, name, val)
+                times = []
+                for n, (k, v, kb, vb) in cases.items():
+                    def restore():
+                        kb.copy_(k)
+                        vb.copy_(v)
+                    g = rs.Graph(kb, vb)
+                    times.append(_time_graph(rs, torch, g, restore, reps))
+                    g.close()
+                res["%d/%d/%d" % (warp_max, small, bits)] = times
+    for name, val in old.items():
+        rs.tune_set_class(0, name, val)
+    best_t = [min(t[i] for t in res.values()) for i in range(2)]
+    best = min(res, key=lambda c: sum(res[c][i] / best_t[i] for i in range(2)))
+    warp_max, small, bits = (int(x) for x in best.split("/"))
+    return {"0": {"warp_max": warp_max, "small_max": small, "small_bits": bits,
+                  "one_chip_ms": res}}
 
-        def restore():
-            kb.copy_(k)
-            vb.copy_(v)
-        g = rs.Graph(kb, vb)
-        res[small] = _time_graph(rs, torch, g, restore, reps)
-        g.close()
-    rs.tune_set_class(0, "small_max", old)
-    return {"0": {"small_max": min(res, key=res.get), "one_cta_ms": res}}
+
+def tune_tiny_segments(rs, torch, inputs, reps=3):
+    """Batches of 2^15 short arrays (sizes log-uniform on [2, 2^12]):
+    one-warp sort threshold (0, 256 or 512) x digit width (4 or 8) for the
+    size class of their average size."""
+    k_np, v_np, off_np = inputs.segmented_batch(1 << 15, 1, 12, seed=11)
+    cls = rs.size_class(k_np.size // (1 << 15))
+    k = torch.from_numpy(k_np.view(np.int32)).cuda()
+    v = torch.from_numpy(v_np.view(np.int32)).cuda()
+    off = torch.from_numpy(off_np.view(np.int32)).cuda()
+    kb, vb = torch.empty_like(k), torch.empty_like(v)
+    old = (rs.tune_get_class(cls, "warp_max"), rs.tune_get_class(cls, "small_bits"))
+    res = {}
+    for warp_max in (0, 256, 512):
+        for bits in (4, 8):
+            rs.tune_set_class(cls, "warp_max", warp_max)
+            rs.tune_set_class(cls, "small_bits", bits)
+
+            def restore():
+                kb.copy_(k)
+                vb.copy_(v)
+            g = rs.Graph(kb, vb, off)
+            res["%d/%d" % (warp_max, bits)] = _time_graph(rs, torch, g, restore, reps)
+            g.close()
+    rs.tune_set_class(cls, "warp_max", old[0])
+    rs.tune_set_class(cls, "small_bits", old[1])
+    best = min(res, key=res.get)
+    warp_max, bits = (int(x) for x in best.split("/"))
+    return {str(cls): {"warp_max": warp_max, "small_bits": bits, "tiny_segments_ms": res}}
 
 
 def tune_segmented(rs, torch, inputs, reps=3, total=1 << 28):
@@ -138,7 +183,7 @@ def apply(table: dict) -> None:
     """Set the library's per-class knobs from a table made by this module."""
     from paper_1008_2849_gb300 import rs
     for cls, knobs in table.get("classes", {}).items():
-        for name in ("tile_pairs", "tile_keys", "tile_seg", "small_max"):
+        for name in ("tile_pairs", "tile_keys", "tile_seg", "small_max", "warp_max", "small_bits"):
             if name in knobs:
                 rs.tune_set_class(int(cls), name, int(knobs[name]))
 
@@ -161,8 +206,10 @@ def main(argv=None) -> int:
     rs.lib()
     classes = tune_whole(rs, torch, inputs, reps=a.reps, quick=a.quick)
     classes.update(tune_one_cta(rs, torch, inputs, reps=a.reps))
-    for cls, best in tune_segmented(rs, torch, inputs, reps=a.reps).items():
-        classes.setdefault(cls, {}).update(best)
+    for part in (tune_segmented(rs, torch, inputs, reps=a.reps),
+                 tune_tiny_segments(rs, torch, inputs, reps=a.reps)):
+        for cls, best in part.items():
+            classes.setdefault(cls, {}).update(best)
     table = {"device": torch.cuda.get_device_name(0), "classes": classes}
     with open(a.out, "w") as f:
         json.dump(table, f, indent=1)

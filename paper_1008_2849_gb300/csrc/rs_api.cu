@@ -155,9 +155,10 @@ rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n) 
 Knobs& knobs() {
     // Defaults chosen by the autotuner on GB300: arrays up to 8192 items take
     // the one-CTA sort; up to 2^20 items tile shape 1 (512 x 8, two CTAs per
-    // SM); larger ones shape 3 (384 x 12, two CTAs per SM).
-    static Knobs k{{{1, 1, 3, 8192}, {1, 1, 3, 4096}, {1, 1, 3, 4096}, {3, 3, 3, 4096},
-                    {3, 3, 3, 4096}, {3, 3, 3, 4096}},
+    // SM); larger ones shape 3 (384 x 12, two CTAs per SM).  Per class:
+    // {tile_pairs, tile_keys, tile_seg, small_max, warp_max, small_bits}.
+    static Knobs k{{{1, 1, 3, 8192, 512, 8}, {1, 1, 3, 4096, 512, 8}, {1, 1, 3, 4096, 512, 8},
+                    {3, 3, 3, 4096, 512, 8}, {3, 3, 3, 4096, 512, 8}, {3, 3, 3, 4096, 512, 8}},
                    kDefaultSpinLimit, 0, 4, 3};
     return k;
 }
@@ -181,6 +182,7 @@ const char* kernel_kind_name(int kind) {
     case KK_SEG_HIST: return "seg_hist";
     case KK_SEG_SCAN: return "seg_scan";
     case KK_SEG_ONESWEEP: return "seg_onesweep";
+    case KK_WARP: return "warp_sort";
     default: return nullptr;
     }
 }
@@ -515,6 +517,14 @@ static rs_status set_class_knob(ClassKnobs& c, int knob, int value) {
         if (value < 0 || value > (int)small_sort_capacity()) return RS_ERR_INVALID_ARG;
         c.small_max = value;
         return RS_OK;
+    case 6:
+        if (value < 0 || value > (int)warp_sort_capacity()) return RS_ERR_INVALID_ARG;
+        c.warp_max = value;
+        return RS_OK;
+    case 7:
+        if (value != 4 && value != 8) return RS_ERR_INVALID_ARG;
+        c.small_bits = value;
+        return RS_OK;
     default: return RS_ERR_INVALID_ARG;
     }
 }
@@ -525,6 +535,8 @@ static int get_class_knob(const ClassKnobs& c, int knob) {
     case 1: return c.tile_keys;
     case 4: return c.small_max;
     case 5: return c.tile_seg;
+    case 6: return c.warp_max;
+    case 7: return c.small_bits;
     default: return -1;
     }
 }

@@ -38,7 +38,8 @@ struct Ctrl {
     uint32_t seg_tiles;            // segmented sorts: tiles of the large segments
     uint32_t small_count;          // segmented sorts: number of small segments
     uint32_t large_count;          // segmented sorts: number of large segments
-    uint32_t pad[4];               // keep hist 64-byte aligned
+    uint32_t tiny_count;           // segmented sorts: number of tiny segments
+    uint32_t pad[3];               // keep hist 64-byte aligned
     uint32_t hist[PASSES][RADIX];  // digit histograms (H)
     uint32_t gofs[PASSES][RADIX];  // first output slot of every bucket (G)
 };

@@ -23,6 +23,7 @@ enum KernelKind : int {
     KK_SEG_HIST = 5,
     KK_SEG_SCAN = 6,
     KK_SEG_ONESWEEP = 7,
+    KK_WARP = 8,
     KK_COUNT
 };
 const char* kernel_kind_name(int kind);
@@ -56,12 +57,15 @@ extern const TileConfig kTileConfigs[NUM_TILE_CONFIGS];
 int smallest_tile();
 
 // Per size class tuning (chosen by the autotuner): tile shapes (indices into
-// kTileConfigs) and the largest array / segment sorted by the one-CTA sort.
+// kTileConfigs), the largest array / segment sorted by the one-warp sort and
+// by the one-CTA sort, and the digit width of those two sorts.
 struct ClassKnobs {
     int tile_pairs;
     int tile_keys;
     int tile_seg;
     int small_max;
+    int warp_max;
+    int small_bits;
 };
 // Size classes by item count (whole array; for a segmented sort the average
 // segment): <= 2^13, <= 2^16, <= 2^20, <= 2^24, <= 2^28, larger.
@@ -125,17 +129,26 @@ rs_status launch_onesweep_pairs(int cfg, bool wide, uint32_t* ka, uint32_t* va, 
                                 const SegView* seg, cudaStream_t stream);
 
 // One-CTA sort in shared memory: of every small segment listed by the
-// segmented planner (off != nullptr), or of the single array [0, single_n)
-// with single_n <= small_sort_capacity().
+// segmented planner (off != nullptr; none longer than max_items), or of the
+// single array [0, single_n) with single_n <= max_items <= small_sort_capacity().
+// bits: digit width, 4 or 8.
 rs_status launch_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
                             const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
-                            uint32_t max_items, cudaStream_t stream);
+                            uint32_t max_items, int bits, cudaStream_t stream);
 uint32_t small_sort_capacity();
+
+// One-warp sort in shared memory: of every tiny segment listed by the
+// segmented planner (off != nullptr), or of the single array [0, single_n)
+// with single_n <= warp_sort_capacity().  bits: digit width, 4 or 8.
+rs_status launch_warp_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                           const uint32_t* tiny_list, const Ctrl* ctrl, uint32_t single_n,
+                           int bits, cudaStream_t stream);
+uint32_t warp_sort_capacity();
 
 // Workspace layout of a segmented sort of n items in num_segments segments.
 struct SegLayout {
-    size_t ctrl, status0, status1, alt_keys, alt_vals, tile_geo, small_list, large_first, gofs,
-        total;
+    size_t ctrl, status0, status1, alt_keys, alt_vals, tile_geo, tiny_list, small_list, large_first,
+        gofs, total;
     uint32_t max_tiles, max_large;
 };
 SegLayout seg_layout_for(size_t n, bool pairs, uint32_t num_segments);

@@ -1,5 +1,5 @@
-// rs_segmented.cu -- host side of the segmented sort and of the one-CTA sort:
-// workspace layout, launch sequence and the small-sort launcher.
+// rs_segmented.cu -- host side of the segmented sort: workspace layout and
+// launch sequence.
 #include "rs_internal.h"
 #include "rs_segmented.cuh"
 
@@ -7,57 +7,10 @@ namespace rs {
 
 namespace {
 
-// One-CTA sort shapes: 256 threads x 16 items (4096) and 512 x 16 (8192).
-template <int THREADS, int ITEMS, bool PAIRS>
-rs_status launch_small_shape(uint32_t* keys, uint32_t* vals, const uint32_t* off,
-                             const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
-                             uint32_t grid, cudaStream_t stream) {
-    constexpr uint32_t CAP = THREADS * ITEMS;
-    constexpr size_t SMEM = ((PAIRS ? 4u : 2u) * CAP + (THREADS / 32) * RADIX) * sizeof(uint32_t);
-    auto kern = k_small_sort<THREADS, ITEMS, PAIRS>;
-    static uint64_t attr_on = 0;  // one bit per device with the attribute set
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
-    if (!((attr_on >> dev) & 1u)) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM) !=
-            cudaSuccess)
-            return RS_ERR_CUDA;
-        attr_on |= 1ull << dev;
-    }
-    note_launch_begin(KK_SMALL, stream);
-    kern<<<grid, THREADS, SMEM, stream>>>(keys, vals, off, small_list, ctrl, single_n);
-    note_launch_end(KK_SMALL, stream);
-    return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
-}
-
 constexpr uint32_t kMinLargeSegment = 4097;  // segments up to 4096 items always take the one-CTA sort
 constexpr int SEG_HIST_THREADS = 512;
 
 }  // namespace
-
-uint32_t small_sort_capacity() { return 8192; }
-
-rs_status launch_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
-                            const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
-                            uint32_t max_items, cudaStream_t stream) {
-    DeviceInfo di;
-    rs_status st = device_info(&di);
-    if (st != RS_OK) return st;
-    // Single array: one CTA.  Segment list: a grid-stride loop over it.
-    const uint32_t grid = off == nullptr ? 1u : (uint32_t)di.sm_count * 4u;
-    const bool pairs = vals != nullptr;
-    if (max_items <= 4096)
-        return pairs ? launch_small_shape<256, 16, true>(keys, vals, off, small_list, ctrl, single_n,
-                                                         grid, stream)
-                     : launch_small_shape<256, 16, false>(keys, vals, off, small_list, ctrl,
-                                                          single_n, grid, stream);
-    if (max_items <= 8192)
-        return pairs ? launch_small_shape<512, 16, true>(keys, vals, off, small_list, ctrl, single_n,
-                                                         grid, stream)
-                     : launch_small_shape<512, 16, false>(keys, vals, off, small_list, ctrl,
-                                                          single_n, grid, stream);
-    return RS_ERR_INVALID_ARG;
-}
 
 SegLayout seg_layout_for(size_t n, bool pairs, uint32_t num_segments) {
     SegLayout L{};
@@ -79,6 +32,8 @@ SegLayout seg_layout_for(size_t n, bool pairs, uint32_t num_segments) {
     if (pairs) off = align_up(off + n * 4, 256);
     L.tile_geo = off;
     off = align_up(off + (size_t)L.max_tiles * 16, 256);
+    L.tiny_list = off;
+    off = align_up(off + (size_t)num_segments * 4, 256);
     L.small_list = off;
     off = align_up(off + (size_t)num_segments * 4, 256);
     L.large_first = off;
@@ -105,6 +60,7 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
     uint32_t* alt_k = reinterpret_cast<uint32_t*>(ws + L.alt_keys);
     uint32_t* alt_v = pairs ? reinterpret_cast<uint32_t*>(ws + L.alt_vals) : nullptr;
     uint4* tile_geo = reinterpret_cast<uint4*>(ws + L.tile_geo);
+    uint32_t* tiny_list = reinterpret_cast<uint32_t*>(ws + L.tiny_list);
     uint32_t* small_list = reinterpret_cast<uint32_t*>(ws + L.small_list);
     uint32_t* large_first = reinterpret_cast<uint32_t*>(ws + L.large_first);
     uint32_t* gofs = reinterpret_cast<uint32_t*>(ws + L.gofs);
@@ -115,19 +71,26 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
     uint32_t small_max = (uint32_t)ck.small_max;
     if (small_max < kMinLargeSegment - 1) small_max = kMinLargeSegment - 1;
     if (small_max > small_sort_capacity()) small_max = small_sort_capacity();
+    uint32_t warp_max = (uint32_t)ck.warp_max;
+    if (warp_max > warp_sort_capacity()) warp_max = warp_sort_capacity();
 
     if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return RS_ERR_CUDA;
     if (L.max_large > 0 &&
         cudaMemsetAsync(gofs, 0, (size_t)L.max_large * PASSES * RADIX * 4, stream) != cudaSuccess)
         return RS_ERR_CUDA;
     note_launch_begin(KK_SEG_PLAN, stream);
-    k_seg_plan<<<1, 1024, 0, stream>>>(offsets, num_segments, n, tile, small_max, ctrl, di.sticky,
-                                       tile_geo, small_list, large_first);
+    k_seg_plan<<<1, 1024, 0, stream>>>(offsets, num_segments, n, tile, warp_max, small_max, ctrl,
+                                       di.sticky, tile_geo, tiny_list, small_list, large_first);
     note_launch_end(KK_SEG_PLAN, stream);
     if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
 
-    // Small segments: independent of the large ones (disjoint ranges).
-    st = launch_small_sort(keys, vals, offsets, small_list, ctrl, 0, small_max, stream);
+    // Tiny and small segments: independent of the large ones (disjoint ranges).
+    if (warp_max >= 2) {
+        st = launch_warp_sort(keys, vals, offsets, tiny_list, ctrl, 0, ck.small_bits, stream);
+        if (st != RS_OK) return st;
+    }
+    st = launch_small_sort(keys, vals, offsets, small_list, ctrl, 0, small_max, ck.small_bits,
+                           stream);
     if (st != RS_OK) return st;
 
     // Large segments: histograms, bucket bases, four scatter passes.

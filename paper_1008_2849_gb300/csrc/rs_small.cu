@@ -1,0 +1,114 @@
+// rs_small.cu -- host launchers of the on-chip sorts (rs_small.cuh): the
+// one-warp sort and the one-CTA sort, each at digit width 4 or 8.
+#include "rs_internal.h"
+#include "rs_small.cuh"
+
+namespace rs {
+
+namespace {
+
+// Raise the dynamic shared-memory limit of `kern` once per device.
+template <typename K>
+rs_status allow_smem(K kern, size_t bytes, uint64_t* attr_on) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
+    if (!((*attr_on >> dev) & 1u)) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess)
+            return RS_ERR_CUDA;
+        *attr_on |= 1ull << dev;
+    }
+    return RS_OK;
+}
+
+// One-CTA sort shapes: 256 threads x 16 items (4096) and 512 x 16 (8192).
+template <int THREADS, int ITEMS, int BITS, bool PAIRS>
+rs_status launch_small_shape(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                             const uint32_t* list, const Ctrl* ctrl, uint32_t single_n,
+                             uint32_t grid, cudaStream_t stream) {
+    constexpr uint32_t CAP = THREADS * ITEMS;
+    constexpr size_t SMEM =
+        ((PAIRS ? 4u : 2u) * CAP + (THREADS / 32) * (1u << BITS)) * sizeof(uint32_t);
+    auto kern = k_small_sort<THREADS, ITEMS, BITS, PAIRS>;
+    static uint64_t attr_on = 0;  // one bit per device with the attribute set
+    rs_status st = allow_smem(kern, SMEM, &attr_on);
+    if (st != RS_OK) return st;
+    note_launch_begin(KK_SMALL, stream);
+    kern<<<grid, THREADS, SMEM, stream>>>(keys, vals, off, list, ctrl, single_n);
+    note_launch_end(KK_SMALL, stream);
+    return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+template <int BITS, bool PAIRS>
+rs_status launch_small_bits(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                            const uint32_t* list, const Ctrl* ctrl, uint32_t single_n,
+                            uint32_t max_items, uint32_t grid, cudaStream_t stream) {
+    if (max_items <= 4096)
+        return launch_small_shape<256, 16, BITS, PAIRS>(keys, vals, off, list, ctrl, single_n, grid,
+                                                        stream);
+    return launch_small_shape<512, 16, BITS, PAIRS>(keys, vals, off, list, ctrl, single_n, grid,
+                                                    stream);
+}
+
+template <int BITS, bool PAIRS>
+rs_status launch_warp_bits(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                           const uint32_t* list, const Ctrl* ctrl, uint32_t single_n,
+                           uint32_t grid, cudaStream_t stream) {
+    using L = WarpSortSmem<WARP_SORT_ITEMS, BITS, PAIRS>;
+    auto kern = k_warp_sort<WARP_SORT_ITEMS, BITS, PAIRS>;
+    static uint64_t attr_on = 0;
+    rs_status st = allow_smem(kern, L::BYTES, &attr_on);
+    if (st != RS_OK) return st;
+    note_launch_begin(KK_WARP, stream);
+    kern<<<grid, WARP_SORT_THREADS, L::BYTES, stream>>>(keys, vals, off, list, ctrl, single_n);
+    note_launch_end(KK_WARP, stream);
+    return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+}  // namespace
+
+uint32_t small_sort_capacity() { return 8192; }
+uint32_t warp_sort_capacity() { return 32 * WARP_SORT_ITEMS; }
+
+rs_status launch_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                            const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
+                            uint32_t max_items, int bits, cudaStream_t stream) {
+    if (max_items > small_sort_capacity()) return RS_ERR_INVALID_ARG;
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
+    // Single array: one CTA.  Segment list: a grid-stride loop over it.
+    const uint32_t grid = off == nullptr ? 1u : (uint32_t)di.sm_count * 4u;
+    const bool pairs = vals != nullptr;
+    if (bits == 4)
+        return pairs ? launch_small_bits<4, true>(keys, vals, off, small_list, ctrl, single_n,
+                                                  max_items, grid, stream)
+                     : launch_small_bits<4, false>(keys, vals, off, small_list, ctrl, single_n,
+                                                   max_items, grid, stream);
+    return pairs ? launch_small_bits<8, true>(keys, vals, off, small_list, ctrl, single_n,
+                                              max_items, grid, stream)
+                 : launch_small_bits<8, false>(keys, vals, off, small_list, ctrl, single_n,
+                                               max_items, grid, stream);
+}
+
+rs_status launch_warp_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
+                           const uint32_t* tiny_list, const Ctrl* ctrl, uint32_t single_n,
+                           int bits, cudaStream_t stream) {
+    if (off == nullptr && single_n > warp_sort_capacity()) return RS_ERR_INVALID_ARG;
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
+    const uint32_t grid = off == nullptr ? 1u : (uint32_t)di.sm_count * 3u;
+    const bool pairs = vals != nullptr;
+    if (bits == 4)
+        return pairs ? launch_warp_bits<4, true>(keys, vals, off, tiny_list, ctrl, single_n, grid,
+                                                 stream)
+                     : launch_warp_bits<4, false>(keys, vals, off, tiny_list, ctrl, single_n, grid,
+                                                  stream);
+    return pairs ? launch_warp_bits<8, true>(keys, vals, off, tiny_list, ctrl, single_n, grid,
+                                             stream)
+                 : launch_warp_bits<8, false>(keys, vals, off, tiny_list, ctrl, single_n, grid,
+                                              stream);
+}
+
+}  // namespace rs

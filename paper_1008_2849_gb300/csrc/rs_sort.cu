@@ -102,8 +102,10 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     rs_status st = device_info(&di);
     if (st != RS_OK) return st;
     const ClassKnobs& ck = knobs().cls[size_class(n)];
+    if (n <= (uint32_t)ck.warp_max && n <= warp_sort_capacity())
+        return launch_warp_sort(keys, vals, nullptr, nullptr, nullptr, n, ck.small_bits, stream);
     if (n <= (uint32_t)ck.small_max && n <= small_sort_capacity())
-        return launch_small_sort(keys, vals, nullptr, nullptr, nullptr, n, n, stream);
+        return launch_small_sort(keys, vals, nullptr, nullptr, nullptr, n, n, ck.small_bits, stream);
     char* ws = static_cast<char*>(workspace);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
     void* status[2] = {ws + L.status0, ws + L.status1};

@@ -1,5 +1,6 @@
-"""GPU parity tests of the segmented sort (and of the one-CTA sort it uses for
-small segments) against the CPU oracle, element by element.
+"""GPU parity tests of the segmented sort (and of the one-warp and one-CTA
+sorts it uses for tiny and small segments) against the CPU oracle, element by
+element.
 
 The segmented sort has no counterpart in the paper: it is the paper's sort
 applied to every segment [off[s], off[s+1]) on its own, which is exactly what
@@ -159,3 +160,63 @@ def test_one_cta_sort_sizes(rs):
             assert np.array_equal(to_host(kd), ko) and np.array_equal(to_host(vd), vo), (n, dist)
     finally:
         rs.tune_set("small_max", old)
+
+
+def _with_knobs(rs, settings, fn):
+    """Run fn() with per-class knobs set in every class, then restore them."""
+    saved = [(c, k, rs.tune_get_class(c, k)) for c in range(6) for k in settings]
+    try:
+        for k, v in settings.items():
+            rs.tune_set(k, v)
+        fn()
+    finally:
+        for c, k, v in saved:
+            rs.tune_set_class(c, k, v)
+
+
+TINY_SIZES = [0, 1, 2, 3, 17, 31, 32, 33, 63, 64, 65, 100, 255, 256, 257, 300, 511, 512, 513,
+              600, 1000, 4096, 4097, 5000, 1, 2, 480]
+
+
+@pytest.mark.parametrize("bits", [4, 8])
+@pytest.mark.parametrize("warp_max", [0, 256, 512])
+def test_tiny_segments_warp_sort(rs, bits, warp_max):
+    """Segments around the one-warp sort's capacity, at both digit widths and
+    with the one-warp sort off, at 256 and at 512 items."""
+    sizes = np.array(TINY_SIZES * 3, dtype=np.uint64)
+    off = inputs.offsets_from_sizes(sizes)
+    n = int(off[-1])
+    for dist in ("uniform", "and4", "low16", "equal"):
+        k = inputs.keys(dist, n, seed=94)
+        v = inputs.index_values(n)
+        _with_knobs(rs, {"warp_max": warp_max, "small_bits": bits},
+                    lambda: _check_segmented(rs, k, v, off))
+        _with_knobs(rs, {"warp_max": warp_max, "small_bits": bits},
+                    lambda: _check_segmented(rs, k, v, off, keys_only=True))
+
+
+@pytest.mark.parametrize("bits", [4, 8])
+def test_whole_small_arrays_both_digit_widths(rs, bits):
+    """Whole arrays taken by the one-warp sort (up to 512 items) and by the
+    one-CTA sort (up to 8192), at digit width 4 and 8."""
+    def run():
+        for n, dist in ((1, "uniform"), (2, "uniform"), (33, "and2"), (100, "equal"),
+                        (512, "uniform"), (513, "low16"), (4096, "and4"), (8192, "uniform"),
+                        (8191, "distinct256")):
+            k = inputs.keys(dist, n, seed=95)
+            v = inputs.index_values(n)
+            kd, vd = to_dev(k), to_dev(v)
+            rs.sort_pairs(kd, vd)
+            ko, vo = oracle.sort_pairs(k, v)
+            assert np.array_equal(to_host(kd), ko) and np.array_equal(to_host(vd), vo), (n, dist)
+            kd = to_dev(k)
+            rs.sort_keys(kd)
+            assert np.array_equal(to_host(kd), ko), (n, dist)
+    _with_knobs(rs, {"warp_max": 512, "small_max": 8192, "small_bits": bits}, run)
+
+
+def test_many_tiny_segments_2pow20(rs):
+    """2^14 segments with sizes log-uniform on [2, 2^9] (every one on the
+    one-warp path): a batch of many short arrays."""
+    k, v, off = inputs.segmented_batch(1 << 14, 1, 9, seed=96)
+    _check_segmented(rs, k, v, off)

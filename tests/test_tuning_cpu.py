@@ -58,3 +58,33 @@ def test_device_generator_matches_numpy_on_cpu():
         a = inputs.keys(dist, 5000, 77)
         b = inputs.keys_torch(dist, 5000, 77, device="cpu").numpy().view(np.uint32)
         assert np.array_equal(a, b), dist
+
+
+def test_knob_table_matches_header(rs):
+    """Every RS_TUNE_* value of include/rs.h has the same number in the binding."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "rs.h")).read()
+    header = {m.group(1).lower(): int(m.group(2))
+              for m in re.finditer(r"RS_TUNE_([A-Z_]+)\s*=\s*(\d+)", text)}
+    assert header == rs.TUNE_KNOBS
+
+
+def test_on_chip_sort_knobs_are_checked(rs):
+    saved = [(c, k, rs.tune_get_class(c, k)) for c in range(6) for k in ("warp_max", "small_bits")]
+    try:
+        for bits in (4, 8):
+            rs.tune_set_class(1, "small_bits", bits)
+            assert rs.tune_get_class(1, "small_bits") == bits
+        for bad in (0, 5, 16):
+            with pytest.raises(rs.RsError):
+                rs.tune_set_class(1, "small_bits", bad)
+        rs.tune_set_class(1, "warp_max", 512)
+        rs.tune_set_class(1, "warp_max", 0)
+        assert rs.tune_get_class(1, "warp_max") == 0
+        with pytest.raises(rs.RsError):
+            rs.tune_set_class(1, "warp_max", 513)
+    finally:
+        for c, k, v in saved:
+            rs.tune_set_class(c, k, v)
