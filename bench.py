@@ -113,6 +113,26 @@ def recorded_traffic():
         return None
 
 
+def link_bandwidths(host_buf, dev, reps: int = 3):
+    """Host->device and device->host GB/s of plain copies of `host_buf`
+    (pinned) on this rank's GPU: the best of `reps` timed copies each."""
+    import torch
+    d = torch.empty_like(host_buf, device=dev)
+    back = torch.empty_like(host_buf).pin_memory()
+    nbytes = host_buf.numel() * host_buf.element_size()
+    out = []
+    for dst, src in ((d, host_buf), (back, d)):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            best = min(best, time.perf_counter() - t0)
+        out.append(nbytes / best / 1e9)
+    return out[0], out[1]
+
+
 def cpu_oracle_rate(seconds_budget: float = 12.0, n_sample: int = 1 << 25):
     """Time the CPU oracle (threaded, all host cores) on a bounded sample of
     the workload: 2^25 uniform pairs (seed 2), value = index."""
@@ -285,6 +305,13 @@ def main():
         e2e = {"value": job_throughput(world, e2e_steps, n, dt), "unit": UNIT,
                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                "api": "rs_sort_pairs_host (pinned host buffers)", "steps": e2e_steps}
+        # The host link bounds this number: time the same bytes through plain
+        # pinned copies, and compare with copies + the device-timed sort in series.
+        h2d, d2h = link_bandwidths(kin, dev)
+        bound_s = 8 * n / (h2d * 1e9) + 8 * n / (d2h * 1e9) + elapsed_ms / 1e3 / args.steps
+        e2e.update({"link_h2d_gbs": h2d, "link_d2h_gbs": d2h,
+                    "serial_bound": n / bound_s,
+                    "frac_of_serial_bound": (e2e["value"] / world) / (n / bound_s)})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

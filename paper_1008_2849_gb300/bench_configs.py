@@ -1,0 +1,111 @@
+"""Benchmarks of the keys-only latency case and of the distribution sweep.
+
+    python -m paper_1008_2849_gb300.bench_configs [--steps K] [--warmup W]
+
+1. Keys only, 2^20 uniform uint32 keys (seed 1), four 8-bit passes: device
+   time of one rs_sort_keys_ex (median of K), so a latency.  The array is
+   4 MiB and stays in L2 between steps: this case is not an HBM roofline case.
+2. Distribution sweep at 2^27 pairs (value = index; seeds 3, 4, ...):
+   uniform; AND of 2, 3 and 4 uniform words; 256 distinct values; all keys
+   equal; sorted; reverse sorted; low 16 bits only.  Each step sorts a fresh
+   copy (1 GiB, larger than L2) with rs_sort_pairs_ex; reported are pairs/s
+   (median step) and the number of scatter passes that ran -- a digit that is
+   the same for every key makes its pass the identity, and it is skipped.
+
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+import sys
+
+import numpy as np
+
+DISTS = ("uniform", "and2", "and3", "and4", "distinct256", "equal", "sorted", "reverse", "low16")
+
+
+def _timed(torch, stream, fn, restore, steps, warmup):
+    times = []
+    for i in range(warmup + steps):
+        restore()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from paper_1008_2849_gb300 import build, inputs, rs
+    build.build_library()
+    rs.lib()
+    stream = torch.cuda.current_stream()
+    out = {"metric": "sort throughput and latency per configuration", "unit": "pairs/s"}
+
+    # 1. keys only, 2^20
+    n = 1 << 20
+    k = torch.from_numpy(inputs.keys("uniform", n, seed=1).view(np.int32)).cuda()
+    kb = torch.empty_like(k)
+    ws = rs.alloc_workspace(n, False)
+    ms = _timed(torch, stream, lambda: rs.sort_keys_ex(kb, ws, stream), lambda: kb.copy_(k),
+                a.steps, a.warmup)
+    rs.check_stream()
+    out["keys_2^20_uniform_seed1"] = {"ms": ms, "keys_per_s": n / (ms / 1e3)}
+    del k, kb, ws
+
+    # 2. distribution sweep, 2^27 pairs
+    n = 1 << 27
+    v = torch.arange(n, dtype=torch.int32, device="cuda")
+    kb, vb = torch.empty_like(v), torch.empty_like(v)
+    ws = rs.alloc_workspace(n, True)
+    sweep = {}
+    for i, dist in enumerate(DISTS):
+        k = torch.from_numpy(inputs.keys(dist, n, seed=3 + i).view(np.int32)).cuda()
+
+        def restore():
+            kb.copy_(k)
+            vb.copy_(v)
+        rs.profile_enable(True)
+        rs.profile_read()
+        ms = _timed(torch, stream, lambda: rs.sort_pairs_ex(kb, vb, ws, stream), restore,
+                    a.steps, a.warmup)
+        launches, _ = rs.profile_read().get("onesweep", (0, 0.0))
+        rs.profile_enable(False)
+        rs.check_stream()
+        # Scatter-pass launches per sort; a launch whose pass is skipped
+        # returns at once (it is still counted as a launch).
+        hist = rs.digit_histograms(k).cpu().numpy().view(np.uint32)
+        sweep[dist] = {"seed": 3 + i, "ms": ms, "pairs_per_s": n / (ms / 1e3),
+                       "passes_executed": _executed_passes(hist, n),
+                       "scatter_launches_per_sort": launches // (a.steps + a.warmup)}
+        del k
+    out["pairs_2^27_distributions"] = sweep
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def _executed_passes(hist, n):
+    """Scatter passes that move data, from the digit histograms: a digit whose
+    histogram has one bucket holding all n keys is the identity and skipped;
+    one identity pass is added back when needed to keep the count even (the
+    result must end in the caller's buffer)."""
+    moving = int(sum(1 for p in range(4) if int(hist[p].max()) != n))
+    return moving + (moving & 1)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
