@@ -16,6 +16,10 @@ Every function follows the paper's definitions:
   counterpart; plain definition).
 * ``sort_pairs_threaded`` -- same result on several host threads, used to time
   the CPU baseline.
+* ``sort_typed`` / ``sort_typed_segmented`` -- stable sorts of signed 32-bit
+  integer keys (by value) and of IEEE-754 binary32 keys (by the totalOrder
+  predicate of IEEE 754-2008 Sec. 5.10): no paper counterpart; a plain merge
+  sort with that comparison.
 
 Every function takes an optional ``lib`` (a library bound by ``_bind``) so that
 the pin tests can also be run against deliberately mutated builds of the C
@@ -68,6 +72,13 @@ def _bind(path: str):
     lib.oracle_sort_pairs_threaded.argtypes = [_u32p, _u32p, _u32p, _u32p,
                                                ctypes.c_size_t, ctypes.c_uint]
     lib.oracle_sort_pairs_threaded.restype = ctypes.c_int
+    if hasattr(lib, "oracle_sort_typed"):  # mutated copies of older sources lack it
+        lib.oracle_sort_typed.argtypes = [_u32p, _u32p, _u32p, _u32p, ctypes.c_size_t,
+                                          ctypes.c_int]
+        lib.oracle_sort_typed.restype = ctypes.c_int
+        lib.oracle_sort_typed_segmented.argtypes = [_u32p, _u32p, _u32p, _u32p, ctypes.c_size_t,
+                                                    _u32p, ctypes.c_uint32, ctypes.c_int]
+        lib.oracle_sort_typed_segmented.restype = ctypes.c_int
     return lib
 
 
@@ -161,4 +172,39 @@ def sort_pairs_threaded(keys, vals, nthreads: int, lib=None):
                                             keys.size, int(nthreads))
     if rc:
         raise MemoryError("oracle_sort_pairs_threaded failed (%d)" % rc)
+    return ko, vo
+
+
+KEY_TYPES = {"u32": 0, "i32": 1, "f32": 2}
+
+
+def sort_typed(keys, vals, key_type: str, lib=None):
+    """Stable ascending sort of 32-bit keys read as ``key_type`` ("u32",
+    "i32" or "f32", given as uint32 bit patterns); returns (keys, vals|None)."""
+    keys = _u32(keys)
+    vals = None if vals is None else _u32(vals)
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    rc = (lib or _load()).oracle_sort_typed(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), keys.size,
+                                            KEY_TYPES[key_type])
+    if rc:
+        raise MemoryError("oracle_sort_typed failed (%d)" % rc)
+    return ko, vo
+
+
+def sort_typed_segmented(keys, vals, offsets, key_type: str, lib=None):
+    """``sort_typed`` inside every segment [offsets[s], offsets[s+1])."""
+    keys = _u32(keys)
+    vals = None if vals is None else _u32(vals)
+    offsets = _u32(offsets)
+    nseg = max(offsets.size - 1, 0)
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    rc = (lib or _load()).oracle_sort_typed_segmented(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo),
+                                                      keys.size, _ptr(offsets), nseg,
+                                                      KEY_TYPES[key_type])
+    if rc == -2:
+        raise ValueError("malformed segment table")
+    if rc:
+        raise MemoryError("oracle_sort_typed_segmented failed (%d)" % rc)
     return ko, vo

@@ -27,6 +27,11 @@
  *   - A threaded variant (per-thread chunk histograms, prefix in
  *     (digit, thread) order, scatter) that yields the identical result; it is
  *     what the CPU baseline times on all host cores.
+ *   - Typed keys (no counterpart in the paper, whose keys are unsigned):
+ *     32-bit two's-complement integers ordered by value, and IEEE-754
+ *     binary32 floats ordered by the totalOrder predicate of IEEE 754-2008
+ *     Sec. 5.10.  These are a plain stable merge sort with that comparison,
+ *     written from the definitions, not from any bit transformation.
  *
  * Everything is written as plain loops, with no blocking, fusion or
  * reordering beyond the counting sort itself.
@@ -222,5 +227,87 @@ int oracle_sort_pairs_threaded(const uint32_t* keys_in, const uint32_t* vals_in,
     memcpy(keys_out, ka, n * sizeof(uint32_t));
     if (vals_in) memcpy(vals_out, va, n * sizeof(uint32_t));
     free(ka); free(kb); free(va); free(vb); free(counts); free(args); free(th);
+    return 0;
+}
+
+
+/* ------------------------------------------------------------------------
+ * Typed keys.  key_type 1: the 32-bit word is a two's-complement integer and
+ * keys are ordered by value.  key_type 2: the word is an IEEE-754 binary32
+ * and keys are ordered by totalOrder (IEEE 754-2008 Sec. 5.10): every
+ * negative-signed encoding before every positive-signed one; among positive
+ * signs a larger magnitude (exponent and significand read as one unsigned
+ * field) comes later, among negative signs earlier.  This places -NaN before
+ * -inf, -0 before +0 and +NaN after +inf, and orders NaNs by payload.
+ * Equal keys keep their input order (the merge takes from the left run on
+ * ties).
+ * ---------------------------------------------------------------------- */
+static int typed_less(uint32_t a, uint32_t b, int key_type) {
+    if (key_type == 1) return (int32_t)a < (int32_t)b;
+    const uint32_t sa = a >> 31, sb = b >> 31;
+    const uint32_t ma = a & 0x7fffffffu, mb = b & 0x7fffffffu;
+    if (sa != sb) return sa > sb;  /* negative sign first */
+    if (sa == 0) return ma < mb;   /* both positive */
+    return ma > mb;                /* both negative */
+}
+
+static void merge_sort_idx(const uint32_t* keys, uint32_t* idx, uint32_t* tmp, size_t lo,
+                           size_t hi, int key_type) {
+    if (hi - lo < 2) return;
+    const size_t mid = lo + (hi - lo) / 2;
+    merge_sort_idx(keys, idx, tmp, lo, mid, key_type);
+    merge_sort_idx(keys, idx, tmp, mid, hi, key_type);
+    size_t i = lo, j = mid, o = lo;
+    while (i < mid && j < hi) {
+        if (typed_less(keys[idx[j]], keys[idx[i]], key_type))
+            tmp[o++] = idx[j++];
+        else
+            tmp[o++] = idx[i++];
+    }
+    while (i < mid) tmp[o++] = idx[i++];
+    while (j < hi) tmp[o++] = idx[j++];
+    memcpy(idx + lo, tmp + lo, (hi - lo) * sizeof(uint32_t));
+}
+
+/* Stable sort of typed keys (key_type 1 or 2; 0 = unsigned, as
+ * oracle_sort_pairs).  Returns 0, -1 on allocation failure, -3 on an unknown
+ * key type. */
+int oracle_sort_typed(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                      uint32_t* vals_out, size_t n, int key_type) {
+    if (key_type == 0) return oracle_sort_pairs(keys_in, vals_in, keys_out, vals_out, n);
+    if (key_type != 1 && key_type != 2) return -3;
+    if (n == 0) return 0;
+    uint32_t* idx = (uint32_t*)malloc(n * sizeof(uint32_t));
+    uint32_t* tmp = (uint32_t*)malloc(n * sizeof(uint32_t));
+    if (!idx || !tmp) {
+        free(idx); free(tmp);
+        return -1;
+    }
+    for (size_t i = 0; i < n; ++i) idx[i] = (uint32_t)i;
+    merge_sort_idx(keys_in, idx, tmp, 0, n, key_type);
+    for (size_t i = 0; i < n; ++i) {
+        keys_out[i] = keys_in[idx[i]];
+        if (vals_in) vals_out[i] = vals_in[idx[i]];
+    }
+    free(idx); free(tmp);
+    return 0;
+}
+
+/* Segmented form of oracle_sort_typed (table rules as for
+ * oracle_sort_pairs_segmented). */
+int oracle_sort_typed_segmented(const uint32_t* keys_in, const uint32_t* vals_in,
+                                uint32_t* keys_out, uint32_t* vals_out, size_t n,
+                                const uint32_t* offsets, uint32_t num_segments, int key_type) {
+    for (uint32_t s = 0; s < num_segments; ++s)
+        if (offsets[s] > offsets[s + 1]) return -2;
+    if (num_segments > 0 && offsets[num_segments] > n) return -2;
+    memcpy(keys_out, keys_in, n * sizeof(uint32_t));
+    if (vals_in) memcpy(vals_out, vals_in, n * sizeof(uint32_t));
+    for (uint32_t s = 0; s < num_segments; ++s) {
+        size_t lo = offsets[s], len = (size_t)offsets[s + 1] - offsets[s];
+        int rc = oracle_sort_typed(keys_in + lo, vals_in ? vals_in + lo : NULL, keys_out + lo,
+                                   vals_out ? vals_out + lo : NULL, len, key_type);
+        if (rc) return rc;
+    }
     return 0;
 }

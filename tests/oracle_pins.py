@@ -208,6 +208,88 @@ def pin_threaded(lib=None):
             assert np.array_equal(ko, ref_k) and np.array_equal(vo, ref_v), (n, t)
 
 
+# ---------------------------------------------------------------------------
+# Typed keys: signed 32-bit integers by value; IEEE-754 binary32 by the
+# totalOrder predicate (IEEE 754-2008 Sec. 5.10).  The paper's keys are
+# unsigned; these pins fix the typed oracle against numpy and against the
+# standard's own listing of the order.
+# ---------------------------------------------------------------------------
+def _golden_float_order():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "float_total_order.txt")
+    words = []
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            words.append(int(line.split()[0], 16))
+    return np.array(words, dtype=np.uint32)
+
+
+def pin_typed_i32_numpy(lib=None):
+    """Signed keys: numpy's stable argsort of the int32 view, with extremes
+    and many duplicates."""
+    k = inputs.keys("uniform", 5000, seed=31)
+    k[::7] = inputs.keys("distinct256", k[::7].size, seed=32)
+    k[:6] = np.array([0x80000000, 0x7FFFFFFF, 0xFFFFFFFF, 0, 1, 0x80000001], dtype=np.uint32)
+    v = inputs.index_values(k.size)
+    ko, vo = oracle.sort_typed(k, v, "i32", lib=lib)
+    order = np.argsort(k.view(np.int32), kind="stable")
+    assert np.array_equal(vo, v[order]) and np.array_equal(ko, k[order])
+
+
+def pin_typed_f32_numpy(lib=None):
+    """Float keys without NaNs or zeros (numpy orders those differently from
+    totalOrder): numpy's stable argsort of the float32 view, across signs,
+    magnitudes from subnormal to infinity, and duplicates."""
+    u = inputs.keys("uniform", 6000, seed=33)
+    exp = (u >> np.uint32(24)) % np.uint32(255)          # never the NaN exponent 255
+    k = (u & np.uint32(0x807FFFFF)) | (exp << np.uint32(23))
+    k[::5] = k[1::5][: k[::5].size]                       # duplicates
+    k[:4] = np.array([0xFF800000, 0x7F800000, 0x00000001, 0x80000001], dtype=np.uint32)
+    k[(k & np.uint32(0x7FFFFFFF)) == 0] = 0x3F800000      # no zeros
+    v = inputs.index_values(k.size)
+    ko, vo = oracle.sort_typed(k, v, "f32", lib=lib)
+    order = np.argsort(k.view(np.float32), kind="stable")
+    assert np.array_equal(vo, v[order]) and np.array_equal(ko, k[order])
+
+
+def pin_typed_f32_total_order(lib=None):
+    """The listed totalOrder sequence, shuffled, comes back in that order."""
+    want = _golden_float_order()
+    for seed in (34, 35, 36):
+        perm = np.argsort(inputs.uniform01(seed, want.size, 0), kind="stable")
+        ko, _ = oracle.sort_typed(want[perm], None, "f32", lib=lib)
+        assert np.array_equal(ko, want)
+
+
+def pin_typed_stability(lib=None):
+    """Equal keys (including repeated -0 and NaN words) keep input order."""
+    base = _golden_float_order()
+    idx = inputs.splitmix32(37, 3000, 0) % np.uint32(base.size)
+    k = base[idx]
+    v = inputs.index_values(k.size)
+    for kt in ("f32", "i32"):
+        ko, vo = oracle.sort_typed(k, v, kt, lib=lib)
+        same = ko[1:] == ko[:-1]
+        assert np.all(vo[1:][same] > vo[:-1][same])
+        assert np.array_equal(np.sort(vo), v)
+
+
+def pin_typed_segmented(lib=None):
+    """Segmented typed sort = the typed sort of every segment on its own."""
+    k = inputs.keys("uniform", 3000, seed=38)
+    v = inputs.index_values(k.size)
+    off = inputs.offsets_from_sizes([0, 1, 700, 2, 1500, 0, 797])
+    for kt in ("i32", "f32"):
+        ko, vo = oracle.sort_typed_segmented(k, v, off, kt, lib=lib)
+        for a, b in zip(off[:-1], off[1:]):
+            ek, ev = oracle.sort_typed(k[a:b], v[a:b], kt, lib=lib)
+            assert np.array_equal(ko[a:b], ek) and np.array_equal(vo[a:b], ev)
+
+
+TYPED_PINS = (pin_typed_i32_numpy, pin_typed_f32_numpy, pin_typed_f32_total_order,
+              pin_typed_stability, pin_typed_segmented)
+
 ALL_PINS = (pin_numpy_stable, pin_bruteforce_tiny, pin_exhaustive_small, pin_invariants,
             pin_special_cases, pin_histograms, pin_counting_pass, pin_segmented,
             pin_threaded)

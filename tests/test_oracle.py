@@ -80,3 +80,43 @@ def test_pins_reject_mutant(name, tmp_path):
         except AssertionError:
             failures.append(pin.__name__)
     assert failures, "no pin rejects mutant %s" % name
+
+
+@pytest.mark.parametrize("pin", oracle_pins.TYPED_PINS, ids=lambda f: f.__name__)
+def test_typed_oracle_pin(pin):
+    pin()
+
+
+TYPED_MUTANTS = {
+    "float_negatives_ascending": ("    return ma > mb;                /* both negative */",
+                                  "    return ma < mb;                /* both negative */"),
+    "signed_read_as_unsigned": ("    if (key_type == 1) return (int32_t)a < (int32_t)b;",
+                                "    if (key_type == 1) return a < b;"),
+    "unstable_merge": ("        if (typed_less(keys[idx[j]], keys[idx[i]], key_type))",
+                       "        if (!typed_less(keys[idx[i]], keys[idx[j]], key_type))"),
+    "zeros_equal": ("    if (sa != sb) return sa > sb;  /* negative sign first */",
+                    "    if (sa != sb) return (ma | mb) != 0 && sa > sb;"),
+    "nan_payload_ignored": ("    const uint32_t ma = a & 0x7fffffffu, mb = b & 0x7fffffffu;",
+                            "    const uint32_t ma = (a & 0x7fffffffu) > 0x7f800000u ? 0x7f800001u : (a & 0x7fffffffu),\n"
+                            "                   mb = (b & 0x7fffffffu) > 0x7f800000u ? 0x7f800001u : (b & 0x7fffffffu);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TYPED_MUTANTS))
+def test_typed_pins_reject_mutant(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "rs_oracle.c")).read()
+    old, new = TYPED_MUTANTS[name]
+    assert src.count(old) == 1, "mutation anchor not found: %s" % name
+    mutated = tmp_path / ("%s.c" % name)
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / ("lib%s.so" % name)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                           "-o", str(so), str(mutated)])
+    lib = oracle._bind(str(so))
+    failures = []
+    for pin in oracle_pins.TYPED_PINS:
+        try:
+            pin(lib)
+        except AssertionError:
+            failures.append(pin.__name__)
+    assert failures, "no pin rejects mutant %s" % name
