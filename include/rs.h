@@ -107,6 +107,28 @@ rs_status rs_sort_pairs_segmented_ex(uint32_t* d_keys, uint32_t* d_vals, size_t 
                                      void* cuda_stream, void* d_workspace,
                                      size_t workspace_bytes);
 
+/* Typed keys (the paper's keys are unsigned; this is its sort applied to an
+ * order-preserving encoding).  The 32-bit words of d_keys are read as:
+ *   RS_KEY_U32  unsigned integers (the calls above);
+ *   RS_KEY_I32  two's-complement integers, ascending by value;
+ *   RS_KEY_F32  IEEE-754 binary32, ascending by the totalOrder predicate of
+ *               IEEE 754-2008 Sec. 5.10: -NaN < -inf < ... < -0 < +0 < ...
+ *               < +inf < +NaN, NaNs by payload.
+ * Every word is mapped onto an unsigned word with the same order as it is
+ * first read and mapped back as it is last written, so the result holds the
+ * caller's own bit patterns, stably sorted (equal keys keep their order).
+ * d_vals may be NULL (keys only).  Otherwise as the _ex calls above, with the
+ * same workspace size; the scatter passes of typed sorts always use tile
+ * shape 3.  An unknown key_type is RS_ERR_INVALID_ARG. */
+typedef enum rs_key_type { RS_KEY_U32 = 0, RS_KEY_I32 = 1, RS_KEY_F32 = 2 } rs_key_type;
+
+rs_status rs_sort_typed_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n, int key_type,
+                           void* cuda_stream, void* d_workspace, size_t workspace_bytes);
+rs_status rs_sort_segmented_typed_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                                     const uint32_t* d_offsets, uint32_t num_segments,
+                                     int key_type, void* cuda_stream, void* d_workspace,
+                                     size_t workspace_bytes);
+
 /* Bytes of device workspace an _ex call needs.  n = total items; with_values
  * = 0 for keys only, 1 for pairs; num_segments = 0 for the unsegmented calls,
  * else the number of segments of a segmented call.  Pure host arithmetic. */

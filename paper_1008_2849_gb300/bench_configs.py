@@ -11,6 +11,8 @@
    copy (1 GiB, larger than L2) with rs_sort_pairs_ex; reported are pairs/s
    (median step) and the number of scatter passes that ran -- a digit that is
    the same for every key makes its pass the identity, and it is skipped.
+3. Typed keys at 2^27 pairs of random 32-bit words (seed 21), read as
+   signed integers and as IEEE floats (rs_sort_typed_ex).
 
 Prints one JSON line.
 """
@@ -94,6 +96,21 @@ def main(argv=None) -> int:
                        "scatter_launches_per_sort": launches // (a.steps + a.warmup)}
         del k
     out["pairs_2^27_distributions"] = sweep
+
+    # 3. typed keys (signed integers, IEEE floats), 2^27 pairs of random words
+    typed = {}
+    for key_type in ("i32", "f32"):
+        k = torch.from_numpy(inputs.keys("uniform", n, seed=21).view(np.int32)).cuda()
+
+        def restore():
+            kb.copy_(k)
+            vb.copy_(v)
+        ms = _timed(torch, stream, lambda: rs.sort_typed_ex(kb, vb, key_type, ws, stream), restore,
+                    a.steps, a.warmup)
+        rs.check_stream()
+        typed[key_type] = {"ms": ms, "pairs_per_s": n / (ms / 1e3)}
+        del k
+    out["pairs_2^27_typed_keys"] = typed
     print(json.dumps(out), flush=True)
     return 0
 

@@ -226,11 +226,13 @@ rs_status rs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, size_t n) {
 }
 
 static rs_status ex_sort(uint32_t* keys, uint32_t* vals, size_t n, void* stream, void* ws,
-                         size_t ws_bytes) {
+                         size_t ws_bytes, int key_type = RS_KEY_U32) {
+    if (key_type < RS_KEY_U32 || key_type > RS_KEY_F32) return RS_ERR_INVALID_ARG;
     rs_status st = check_sort_args(keys, vals, n);
     if (st != RS_OK || n == 0) return st;
     if (ws_bytes < layout_for(n, vals != nullptr).total || ws == nullptr) return RS_ERR_INVALID_ARG;
-    return enqueue_sort(keys, vals, (uint32_t)n, static_cast<cudaStream_t>(stream), ws, ws_bytes);
+    return enqueue_sort(keys, vals, (uint32_t)n, static_cast<cudaStream_t>(stream), ws, ws_bytes,
+                        (uint32_t)key_type);
 }
 
 rs_status rs_sort_keys_ex(uint32_t* d_keys, size_t n, void* cuda_stream, void* d_workspace,
@@ -284,13 +286,29 @@ rs_status rs_sort_pairs_segmented(uint32_t* d_keys, uint32_t* d_vals, size_t n,
 }
 
 static rs_status ex_segmented(uint32_t* keys, uint32_t* vals, size_t n, const uint32_t* offsets,
-                              uint32_t num_segments, void* stream, void* ws, size_t ws_bytes) {
+                              uint32_t num_segments, void* stream, void* ws, size_t ws_bytes,
+                              int key_type = RS_KEY_U32) {
+    if (key_type < RS_KEY_U32 || key_type > RS_KEY_F32) return RS_ERR_INVALID_ARG;
     rs_status st = seg_args(keys, vals, n, offsets, num_segments);
     if (st != RS_OK || n == 0 || num_segments == 0) return st;
     if (ws == nullptr || ws_bytes < seg_layout_for(n, vals != nullptr, num_segments).total)
         return RS_ERR_INVALID_ARG;
     return enqueue_sort_segmented(keys, vals, (uint32_t)n, offsets, num_segments,
-                                  static_cast<cudaStream_t>(stream), ws, ws_bytes);
+                                  static_cast<cudaStream_t>(stream), ws, ws_bytes,
+                                  (uint32_t)key_type);
+}
+
+rs_status rs_sort_typed_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n, int key_type,
+                           void* cuda_stream, void* d_workspace, size_t workspace_bytes) {
+    return ex_sort(d_keys, d_vals, n, cuda_stream, d_workspace, workspace_bytes, key_type);
+}
+
+rs_status rs_sort_segmented_typed_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n,
+                                     const uint32_t* d_offsets, uint32_t num_segments,
+                                     int key_type, void* cuda_stream, void* d_workspace,
+                                     size_t workspace_bytes) {
+    return ex_segmented(d_keys, d_vals, n, d_offsets, num_segments, cuda_stream, d_workspace,
+                        workspace_bytes, key_type);
 }
 
 rs_status rs_sort_keys_segmented_ex(uint32_t* d_keys, size_t n, const uint32_t* d_offsets,

@@ -44,6 +44,27 @@ struct Ctrl {
     uint32_t gofs[PASSES][RADIX];  // first output slot of every bucket (G)
 };
 
+// Key types.  A typed key is mapped onto an unsigned word with the same
+// order before its digits are read, and mapped back when it is stored:
+//   KEY_I32  two's-complement integers by value: flip the sign bit;
+//   KEY_F32  IEEE-754 binary32 by totalOrder (IEEE 754-2008 Sec. 5.10): a
+//            positive-signed word gets its sign bit set, a negative-signed
+//            word is complemented (larger magnitude -> smaller word).
+// Both maps are bijections on 32-bit words, so sorting the mapped words
+// stably and mapping back is the stable sort in the typed order.
+constexpr uint32_t KEY_U32 = 0;
+constexpr uint32_t KEY_I32 = 1;
+constexpr uint32_t KEY_F32 = 2;
+
+__device__ __forceinline__ uint32_t key_to_ordered(uint32_t k, uint32_t type) {
+    const uint32_t neg = type == KEY_F32 ? (uint32_t)((int32_t)k >> 31) : 0u;
+    return k ^ (neg | (type != KEY_U32 ? 0x80000000u : 0u));
+}
+__device__ __forceinline__ uint32_t key_from_ordered(uint32_t k, uint32_t type) {
+    const uint32_t neg = type == KEY_F32 ? ~(uint32_t)((int32_t)k >> 31) : 0u;
+    return k ^ (neg | (type != KEY_U32 ? 0x80000000u : 0u));
+}
+
 // Status words of the decoupled look-back: a 2-bit flag above a count.
 //   flag 0 = nothing published, AGG = this tile's own count,
 //   INC = inclusive prefix over this tile and all tiles before it.

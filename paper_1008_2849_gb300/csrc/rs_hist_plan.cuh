@@ -34,7 +34,7 @@ constexpr int HIST_COLUMNS = 3;  // k_hist4_cols
 template <int THREADS, int MODE>
 __global__ void __launch_bounds__(THREADS)
 k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
-        uint4* __restrict__ clear, uint32_t clear_vec4) {
+        uint4* __restrict__ clear, uint32_t clear_vec4, uint32_t key_type) {
     __shared__ uint32_t s_h[PASSES * RADIX];
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31;
@@ -52,6 +52,7 @@ k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hi
     const uint4* __restrict__ body = reinterpret_cast<const uint4*>(keys + head);
 
     auto count_key = [&](uint32_t key, bool ok) {
+        key = key_to_ordered(key, key_type);
 #pragma unroll
         for (uint32_t p = 0; p < PASSES; ++p) {
             const uint32_t d = (key >> (p * RADIX_BITS)) & (RADIX - 1);
@@ -89,7 +90,7 @@ k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hi
         const uint32_t i = tid < 4 ? tid : tail + (tid - 4);
         const bool ok = tid < 4 ? i < head : i < n;
         if (ok) {
-            const uint32_t key = keys[i];
+            const uint32_t key = key_to_ordered(keys[i], key_type);
 #pragma unroll
             for (uint32_t p = 0; p < PASSES; ++p)
                 atomicAdd(&s_h[p * RADIX + ((key >> (p * RADIX_BITS)) & (RADIX - 1))], 1u);
@@ -115,7 +116,7 @@ constexpr uint32_t HIST_COL_WORDS = PASSES * RADIX * 32;
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
 k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
-             uint4* __restrict__ clear, uint32_t clear_vec4) {
+             uint4* __restrict__ clear, uint32_t clear_vec4, uint32_t key_type) {
     extern __shared__ uint4 s_cols4[];
     uint32_t* const s_col = reinterpret_cast<uint32_t*>(s_cols4);
     const uint32_t tid = threadIdx.x;
@@ -133,6 +134,7 @@ k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
     const uint4* __restrict__ body = reinterpret_cast<const uint4*>(keys + head);
     uint32_t* const mycol = s_col + lane;
     auto count_key = [&](uint32_t key) {
+        key = key_to_ordered(key, key_type);
 #pragma unroll
         for (uint32_t p = 0; p < PASSES; ++p)
             atomicAdd(mycol + ((p * RADIX + ((key >> (p * RADIX_BITS)) & (RADIX - 1))) << 5), 1u);

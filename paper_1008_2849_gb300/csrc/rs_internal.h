@@ -55,6 +55,9 @@ constexpr int NUM_TILE_CONFIGS = 0 RS_TILE_SHAPES(RS_COUNT_SHAPE);
 #undef RS_COUNT_SHAPE
 extern const TileConfig kTileConfigs[NUM_TILE_CONFIGS];
 int smallest_tile();
+// Sorts of typed keys run their scatter passes with this shape (the default
+// of large arrays); only it is compiled with the key maps.
+constexpr int kTypedShape = 3;
 
 // Per size class tuning (chosen by the autotuner): tile shapes (indices into
 // kTileConfigs), the largest array / segment sorted by the one-warp sort and
@@ -104,7 +107,7 @@ Layout layout_for(size_t n, bool pairs);
 // Enqueue the whole sort of n items (1 <= n < 2^32) on `stream`, using the
 // caller's workspace (at least layout_for(n, pairs).total bytes).
 rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
-                       void* workspace, size_t workspace_bytes);
+                       void* workspace, size_t workspace_bytes, uint32_t key_type = 0);
 
 // Enqueue the digit histograms of n keys into hist[4 * 256] (zeroed first).
 rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
@@ -120,13 +123,15 @@ struct SegView {
 
 // Scatter-pass launchers, one per value flavour (separate translation units);
 // seg == nullptr for the unsegmented sort.
+// key_type: KEY_U32, KEY_I32 or KEY_F32 (rs_device.cuh).
 rs_status launch_onesweep_keys(int cfg, bool wide, uint32_t* ka, uint32_t* kb, uint32_t n,
                                uint32_t pass, Ctrl* ctrl, uint32_t* sticky, void* status,
-                               void* status_clear, const SegView* seg, cudaStream_t stream);
+                               void* status_clear, const SegView* seg, uint32_t key_type,
+                               cudaStream_t stream);
 rs_status launch_onesweep_pairs(int cfg, bool wide, uint32_t* ka, uint32_t* va, uint32_t* kb,
                                 uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
                                 uint32_t* sticky, void* status, void* status_clear,
-                                const SegView* seg, cudaStream_t stream);
+                                const SegView* seg, uint32_t key_type, cudaStream_t stream);
 
 // One-CTA sort in shared memory: of every small segment listed by the
 // segmented planner (off != nullptr; none longer than max_items), or of the
@@ -134,7 +139,7 @@ rs_status launch_onesweep_pairs(int cfg, bool wide, uint32_t* ka, uint32_t* va, 
 // bits: digit width, 4 or 8.
 rs_status launch_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
                             const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
-                            uint32_t max_items, int bits, cudaStream_t stream);
+                            uint32_t max_items, int bits, uint32_t key_type, cudaStream_t stream);
 uint32_t small_sort_capacity();
 
 // One-warp sort in shared memory: of every tiny segment listed by the
@@ -142,7 +147,7 @@ uint32_t small_sort_capacity();
 // with single_n <= warp_sort_capacity().  bits: digit width, 4 or 8.
 rs_status launch_warp_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
                            const uint32_t* tiny_list, const Ctrl* ctrl, uint32_t single_n,
-                           int bits, cudaStream_t stream);
+                           int bits, uint32_t key_type, cudaStream_t stream);
 uint32_t warp_sort_capacity();
 
 // Workspace layout of a segmented sort of n items in num_segments segments.
@@ -154,7 +159,8 @@ struct SegLayout {
 SegLayout seg_layout_for(size_t n, bool pairs, uint32_t num_segments);
 rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
                                  const uint32_t* offsets, uint32_t num_segments,
-                                 cudaStream_t stream, void* workspace, size_t workspace_bytes);
+                                 cudaStream_t stream, void* workspace, size_t workspace_bytes,
+                                 uint32_t key_type = 0);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -82,18 +82,25 @@ struct OnesweepSmem {
 //     so consecutive threads store consecutive addresses of one bucket run.
 //     Every global store is checked against n (ERR_BOUNDS instead of a fault).
 // ---------------------------------------------------------------------------
+// Typed keys (TYPED): the first pass that moves data maps every key it reads
+// onto its ordered unsigned word (key_to_ordered), so all digits, ranks and
+// staged keys of the sort are those of the ordered words, and the last pass
+// maps every key it stores back (key_from_ordered).  Values are untouched.
+//
 // Segmented sorts (SEG): tiles never straddle a segment.  tile_geo[t] =
 // (first item, item count, first tile of its segment, segment) for every tile
 // of the large segments; seg_gofs[s][pass][b] is the absolute first output
 // slot of bucket b of segment s; the number of tiles is ctrl->seg_tiles.
-template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WINDOW, bool SEG>
+template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WINDOW, bool SEG,
+          bool TYPED>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
            uint32_t* __restrict__ kb, uint32_t* __restrict__ vb,
            uint32_t n, uint32_t pass, uint32_t num_tiles, Ctrl* __restrict__ ctrl,
            uint32_t* __restrict__ sticky, S* __restrict__ status, S* __restrict__ status_clear,
            uint32_t clear_words, uint32_t spin_limit, uint32_t debug,
-           const uint4* __restrict__ tile_geo, const uint32_t* __restrict__ seg_gofs) {
+           const uint4* __restrict__ tile_geo, const uint32_t* __restrict__ seg_gofs,
+           uint32_t key_type) {
     using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
     using SW = StatusWord<S>;
     static_assert(THREADS >= (int)RADIX && THREADS % 32 == 0, "one thread per digit");
@@ -144,6 +151,20 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 status_clear[i] = 0;
         return;
     }
+    // Typed keys: map on reading in the first executed pass, back on storing
+    // in the last one (the plan in ctrl->dir says which passes execute).
+    uint32_t map_in = KEY_U32, map_out = KEY_U32;
+    if (TYPED) {
+        bool first = true, last = true;
+        for (uint32_t q = 0; q < PASSES; ++q) {
+            if (ctrl->dir[q] == DIR_SKIP) continue;
+            if (q < pass) first = false;
+            if (q > pass) last = false;
+        }
+        map_in = first ? key_type : KEY_U32;
+        map_out = last ? key_type : KEY_U32;
+    }
+    auto read_key = [map_in](uint32_t k) { return TYPED ? key_to_ordered(k, map_in) : k; };
     const uint32_t* __restrict__ src_k = dir == DIR_A_TO_B ? ka : kb;
     uint32_t* __restrict__ dst_k = dir == DIR_A_TO_B ? kb : ka;
     const uint32_t* __restrict__ src_v = dir == DIR_A_TO_B ? va : vb;
@@ -223,12 +244,12 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         if (valid == TILE) {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)
-                atomicAdd(&row[digit_of(keys[j * 32])], 1u);
+                atomicAdd(&row[digit_of(read_key(keys[j * 32]))], 1u);
         } else {
             const uint32_t left = valid > w * WARP_ITEMS ? valid - w * WARP_ITEMS : 0u;
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)
-                if (j * 32 + lane < left) atomicAdd(&row[digit_of(keys[j * 32])], 1u);
+                if (j * 32 + lane < left) atomicAdd(&row[digit_of(read_key(keys[j * 32]))], 1u);
         }
     };
     // Threads < 256 only, once the per-warp counts of tile t are in wcnt:
@@ -323,7 +344,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             for (int j = 0; j < ITEMS; ++j) {
                 const bool is_live = FULL || j * 32 + lane < left;
                 const uint32_t live = FULL ? 0xffffffffu : prefix_lanes(j * 32, left);
-                const uint32_t k = keys[j * 32];
+                const uint32_t k = read_key(keys[j * 32]);
                 const uint32_t d = digit_of(k);
                 uint32_t peers;
                 if (j & 1) {
@@ -472,16 +493,18 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                     const uint32_t kk = s_stage[s];
                     const uint32_t g = s_gofs[digit_of(kk)] + s;
                     if (g < n) {
-                        dst_k[g] = kk;
+                        dst_k[g] = TYPED ? key_from_ordered(kk, map_out) : kk;
                         if (PAIRS) dst_v[g] = in_k[s];
                     } else {
                         bad = true;
                     }
                 }
             };
-            if (FREE > 0 && tid >= RADIX) {
+            if constexpr (FREE > 0) {
+                if (tid >= RADIX) {
 #pragma unroll
-                for (uint32_t k = 0; k < EARLY_PER; ++k) store_slot(k * FREE + (tid - RADIX));
+                    for (uint32_t k = 0; k < EARLY_PER; ++k) store_slot(k * FREE + (tid - RADIX));
+                }
             }
 #pragma unroll
             for (uint32_t k = 0; k < LATE_PER; ++k) {

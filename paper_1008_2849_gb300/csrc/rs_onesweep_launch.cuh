@@ -7,14 +7,24 @@
 
 namespace rs {
 
-template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S, bool SEG>
+// Compile-time parameters of tile shape I of RS_TILE_SHAPES.
+template <int I> struct TileShape;
+#define RS_SHAPE_STRUCT(I, T, J, B, W)                                                    \
+    template <> struct TileShape<I> {                                                     \
+        static constexpr int threads = T, items = J, min_blocks = B, window = W;          \
+    };
+RS_TILE_SHAPES(RS_SHAPE_STRUCT)
+#undef RS_SHAPE_STRUCT
+
+template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S, bool SEG,
+          bool TYPED>
 static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
                                        uint32_t n, uint32_t pass, Ctrl* ctrl, uint32_t* sticky,
                                        void* status, void* status_clear, const SegView& seg,
-                                       cudaStream_t stream) {
+                                       uint32_t key_type, cudaStream_t stream) {
     using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
     constexpr uint32_t TILE = L::TILE;
-    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW, SEG>;
+    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW, SEG, TYPED>;
     static int ctas_per_sm[64] = {0};  // per device: resident CTAs per SM
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
@@ -41,22 +51,28 @@ static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb,
     kern<<<grid, THREADS, L::BYTES, stream>>>(ka, va, kb, vb, n, pass, tiles, ctrl, sticky,
                                               static_cast<S*>(status), static_cast<S*>(status_clear),
                                               tiles * RADIX, knobs().spin_limit, knobs().debug,
-                                              seg.tile_geo, seg.gofs);
+                                              seg.tile_geo, seg.gofs, key_type);
     note_launch_end(SEG ? KK_SEG_ONESWEEP : KK_ONESWEEP, stream);
     return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
 template <bool PAIRS, typename S, bool SEG>
-static rs_status launch_onesweep_typed(int cfg, uint32_t* ka, uint32_t* va, uint32_t* kb,
-                                       uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
-                                       uint32_t* sticky, void* status, void* status_clear,
-                                       const SegView& seg, cudaStream_t stream) {
+static rs_status launch_onesweep_variant(int cfg, uint32_t* ka, uint32_t* va, uint32_t* kb,
+                                         uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
+                                         uint32_t* sticky, void* status, void* status_clear,
+                                         const SegView& seg, uint32_t key_type,
+                                         cudaStream_t stream) {
+    if (key_type != KEY_U32) {
+        using T = TileShape<kTypedShape>;
+        return launch_onesweep_shape<T::threads, T::items, T::min_blocks, T::window, PAIRS, S, SEG,
+                                     true>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
+                                           status_clear, seg, key_type, stream);
+    }
     switch (cfg) {
 #define RS_CASE(I, T, J, B, W)                                                                    \
     case I:                                                                                       \
-        return launch_onesweep_shape<T, J, B, W, PAIRS, S, SEG>(ka, va, kb, vb, n, pass, ctrl,    \
-                                                                sticky, status, status_clear,     \
-                                                                seg, stream);
+        return launch_onesweep_shape<T, J, B, W, PAIRS, S, SEG, false>(                           \
+            ka, va, kb, vb, n, pass, ctrl, sticky, status, status_clear, seg, KEY_U32, stream);
         RS_TILE_SHAPES(RS_CASE)
 #undef RS_CASE
     default: return RS_ERR_INVALID_ARG;

@@ -46,7 +46,9 @@ SegLayout seg_layout_for(size_t n, bool pairs, uint32_t num_segments) {
 
 rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
                                  const uint32_t* offsets, uint32_t num_segments,
-                                 cudaStream_t stream, void* workspace, size_t workspace_bytes) {
+                                 cudaStream_t stream, void* workspace, size_t workspace_bytes,
+                                 uint32_t key_type) {
+    if (key_type > KEY_F32) return RS_ERR_INVALID_ARG;
     const bool pairs = vals != nullptr;
     const SegLayout L = seg_layout_for(n, pairs, num_segments);
     if (workspace == nullptr || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
@@ -66,7 +68,7 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
     uint32_t* gofs = reinterpret_cast<uint32_t*>(ws + L.gofs);
 
     const ClassKnobs& ck = knobs().cls[size_class(n / num_segments)];
-    const int cfg = ck.tile_seg;
+    const int cfg = key_type != KEY_U32 ? kTypedShape : ck.tile_seg;
     const uint32_t tile = (uint32_t)(kTileConfigs[cfg].threads * kTileConfigs[cfg].items);
     uint32_t small_max = (uint32_t)ck.small_max;
     if (small_max < kMinLargeSegment - 1) small_max = kMinLargeSegment - 1;
@@ -86,18 +88,19 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
 
     // Tiny and small segments: independent of the large ones (disjoint ranges).
     if (warp_max >= 2) {
-        st = launch_warp_sort(keys, vals, offsets, tiny_list, ctrl, 0, ck.small_bits, stream);
+        st = launch_warp_sort(keys, vals, offsets, tiny_list, ctrl, 0, ck.small_bits, key_type,
+                              stream);
         if (st != RS_OK) return st;
     }
     st = launch_small_sort(keys, vals, offsets, small_list, ctrl, 0, small_max, ck.small_bits,
-                           stream);
+                           key_type, stream);
     if (st != RS_OK) return st;
 
     // Large segments: histograms, bucket bases, four scatter passes.
     note_launch_begin(KK_SEG_HIST, stream);
     k_seg_hist<SEG_HIST_THREADS><<<di.sm_count * 2, SEG_HIST_THREADS, 0, stream>>>(
         keys, ctrl, tile_geo, gofs, static_cast<uint4*>(status[0]),
-        (uint32_t)((L.status1 - L.status0) / sizeof(uint4)));
+        (uint32_t)((L.status1 - L.status0) / sizeof(uint4)), key_type);
     note_launch_end(KK_SEG_HIST, stream);
     note_launch_begin(KK_SEG_SCAN, stream);
     k_seg_scan<<<di.sm_count * 2, 1024, 0, stream>>>(ctrl, gofs, large_first);
@@ -112,9 +115,9 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
         void* cur = status[p & 1];
         void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;
         st = pairs ? launch_onesweep_pairs(cfg, false, keys, vals, alt_k, alt_v, n, p, ctrl,
-                                           di.sticky, cur, next, &view, stream)
+                                           di.sticky, cur, next, &view, key_type, stream)
                    : launch_onesweep_keys(cfg, false, keys, alt_k, n, p, ctrl, di.sticky, cur, next,
-                                          &view, stream);
+                                          &view, key_type, stream);
         if (st != RS_OK) return st;
     }
     return RS_OK;

@@ -119,7 +119,7 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_seg_hist(const uint32_t* __restrict__ keys, const Ctrl* __restrict__ ctrl,
            const uint4* __restrict__ tile_geo, uint32_t* __restrict__ hist,
-           uint4* __restrict__ clear, uint32_t clear_vec4) {
+           uint4* __restrict__ clear, uint32_t clear_vec4, uint32_t key_type) {
     __shared__ uint32_t s_h[PASSES * RADIX];
     const uint32_t tid = threadIdx.x;
     for (uint32_t i = blockIdx.x * THREADS + tid; i < clear_vec4; i += gridDim.x * THREADS)
@@ -147,7 +147,7 @@ k_seg_hist(const uint32_t* __restrict__ keys, const Ctrl* __restrict__ ctrl,
             cur = g.w;
         }
         for (uint32_t i = tid; i < g.y; i += THREADS) {
-            const uint32_t k = ld_stream(keys + g.x + i);
+            const uint32_t k = key_to_ordered(ld_stream(keys + g.x + i), key_type);
 #pragma unroll
             for (uint32_t p = 0; p < PASSES; ++p)
                 atomicAdd(&s_h[p * RADIX + ((k >> (p * RADIX_BITS)) & (RADIX - 1))], 1u);

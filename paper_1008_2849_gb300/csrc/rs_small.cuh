@@ -5,7 +5,8 @@
 // BITS is a template parameter: 8 bits (four passes, 256 buckets, as in the
 // scatter passes) or 4 bits (eight passes, 16 buckets) -- which is faster
 // depends on the array size, and the autotuner picks it per size class.
-// Either width gives the same stable order.
+// Either width gives the same stable order.  Typed keys (key_type) are mapped
+// onto their ordered words when read and back when written.
 #pragma once
 
 #include "rs_device.cuh"
@@ -47,7 +48,7 @@ template <int ITEMS, int BITS, bool PAIRS>
 __global__ void __launch_bounds__(WARP_SORT_THREADS)
 k_warp_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
             const uint32_t* __restrict__ off, const uint32_t* __restrict__ list,
-            const Ctrl* __restrict__ ctrl, uint32_t single_n) {
+            const Ctrl* __restrict__ ctrl, uint32_t single_n, uint32_t key_type) {
     using L = WarpSortSmem<ITEMS, BITS, PAIRS>;
     constexpr uint32_t NB = 1u << BITS;
     constexpr uint32_t NPASS = 32 / BITS;
@@ -75,7 +76,7 @@ k_warp_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
             m = off[s + 1] - lo;
         }
         for (uint32_t i = lane; i < m; i += 32) {
-            s_k[i] = keys[lo + i];
+            s_k[i] = key_to_ordered(keys[lo + i], key_type);
             if (PAIRS) s_v[i] = vals[lo + i];
         }
         uint32_t cur = 0;
@@ -142,7 +143,7 @@ k_warp_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
         const uint32_t* fk = s_k + cur * CAP;
         const uint32_t* fv = s_v + cur * CAP;
         for (uint32_t i = lane; i < m; i += 32) {
-            keys[lo + i] = fk[i];
+            keys[lo + i] = key_from_ordered(fk[i], key_type);
             if (PAIRS) vals[lo + i] = fv[i];
         }
         __syncwarp();
@@ -163,7 +164,7 @@ template <int THREADS, int ITEMS, int BITS, bool PAIRS>
 __global__ void __launch_bounds__(THREADS)
 k_small_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
              const uint32_t* __restrict__ off, const uint32_t* __restrict__ small_list,
-             const Ctrl* __restrict__ ctrl, uint32_t single_n) {
+             const Ctrl* __restrict__ ctrl, uint32_t single_n, uint32_t key_type) {
     constexpr uint32_t NB = 1u << BITS;
     constexpr uint32_t NPASS = 32 / BITS;
     constexpr uint32_t NW = (NB + 31) / 32;  // warps holding digit totals
@@ -195,7 +196,7 @@ k_small_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
             m = off[s + 1] - lo;
         }
         for (uint32_t i = tid; i < m; i += THREADS) {
-            s_k[i] = keys[lo + i];
+            s_k[i] = key_to_ordered(keys[lo + i], key_type);
             if (PAIRS) s_v[i] = vals[lo + i];
         }
         __syncthreads();
@@ -268,7 +269,7 @@ k_small_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
         const uint32_t* fk = s_k + cur * CAP;
         const uint32_t* fv = s_v + cur * CAP;
         for (uint32_t i = tid; i < m; i += THREADS) {
-            keys[lo + i] = fk[i];
+            keys[lo + i] = key_from_ordered(fk[i], key_type);
             if (PAIRS) vals[lo + i] = fv[i];
         }
         __syncthreads();

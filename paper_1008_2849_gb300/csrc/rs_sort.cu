@@ -42,7 +42,7 @@ Layout layout_for(size_t n, bool pairs) {
 }
 
 static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, void* clear,
-                             size_t clear_bytes, cudaStream_t stream) {
+                             size_t clear_bytes, uint32_t key_type, cudaStream_t stream) {
     DeviceInfo di;
     rs_status st = device_info(&di);
     if (st != RS_OK) return st;
@@ -68,7 +68,8 @@ static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, v
         if (grid > need) grid = need > 0 ? need : 1;
         note_launch_begin(KK_HIST, stream);
         k_hist4_cols<T><<<grid, T, SMEM, stream>>>(keys, n, hist, static_cast<uint4*>(clear),
-                                                    (uint32_t)(clear_bytes / sizeof(uint4)));
+                                                    (uint32_t)(clear_bytes / sizeof(uint4)),
+                                                    key_type);
         note_launch_end(KK_HIST, stream);
         return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
     }
@@ -80,7 +81,7 @@ static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, v
     }
     note_launch_begin(KK_HIST, stream);
     kern<<<blocks, HIST_THREADS, 0, stream>>>(keys, n, hist, static_cast<uint4*>(clear),
-                                              (uint32_t)(clear_bytes / sizeof(uint4)));
+                                              (uint32_t)(clear_bytes / sizeof(uint4)), key_type);
     note_launch_end(KK_HIST, stream);
     return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
@@ -89,11 +90,12 @@ rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
                              cudaStream_t stream) {
     if (cudaMemsetAsync(hist, 0, PASSES * RADIX * sizeof(uint32_t), stream) != cudaSuccess)
         return RS_ERR_CUDA;
-    return launch_hist(keys, n, hist, nullptr, 0, stream);
+    return launch_hist(keys, n, hist, nullptr, 0, KEY_U32, stream);
 }
 
 rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
-                       void* workspace, size_t workspace_bytes) {
+                       void* workspace, size_t workspace_bytes, uint32_t key_type) {
+    if (key_type > KEY_F32) return RS_ERR_INVALID_ARG;
     const bool pairs = vals != nullptr;
     const Layout L = layout_for(n, pairs);
     if (workspace == nullptr || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
@@ -103,9 +105,11 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     if (st != RS_OK) return st;
     const ClassKnobs& ck = knobs().cls[size_class(n)];
     if (n <= (uint32_t)ck.warp_max && n <= warp_sort_capacity())
-        return launch_warp_sort(keys, vals, nullptr, nullptr, nullptr, n, ck.small_bits, stream);
+        return launch_warp_sort(keys, vals, nullptr, nullptr, nullptr, n, ck.small_bits, key_type,
+                                stream);
     if (n <= (uint32_t)ck.small_max && n <= small_sort_capacity())
-        return launch_small_sort(keys, vals, nullptr, nullptr, nullptr, n, n, ck.small_bits, stream);
+        return launch_small_sort(keys, vals, nullptr, nullptr, nullptr, n, n, ck.small_bits,
+                                 key_type, stream);
     char* ws = static_cast<char*>(workspace);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
     void* status[2] = {ws + L.status0, ws + L.status1};
@@ -114,7 +118,7 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     uint32_t* alt_v = pairs ? reinterpret_cast<uint32_t*>(ws + L.alt_vals) : nullptr;
 
     if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return RS_ERR_CUDA;
-    st = launch_hist(keys, n, &ctrl->hist[0][0], status[0], status_bytes, stream);
+    st = launch_hist(keys, n, &ctrl->hist[0][0], status[0], status_bytes, key_type, stream);
     if (st != RS_OK) return st;
     note_launch_begin(KK_PLAN, stream);
     k_plan<<<1, 1024, 0, stream>>>(ctrl, n);
@@ -126,9 +130,9 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
         void* cur = status[p & 1];
         void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;
         st = pairs ? launch_onesweep_pairs(cfg, L.wide_status, keys, vals, alt_k, alt_v, n, p, ctrl,
-                                           di.sticky, cur, next, nullptr, stream)
+                                           di.sticky, cur, next, nullptr, key_type, stream)
                    : launch_onesweep_keys(cfg, L.wide_status, keys, alt_k, n, p, ctrl, di.sticky,
-                                          cur, next, nullptr, stream);
+                                          cur, next, nullptr, key_type, stream);
         if (st != RS_OK) return st;
     }
     return RS_OK;

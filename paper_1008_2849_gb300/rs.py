@@ -42,6 +42,8 @@ SIGNATURES = {
     "rs_sort_pairs_segmented": (_int, [_vp, _vp, _sz, _vp, _u32]),
     "rs_sort_keys_segmented_ex": (_int, [_vp, _sz, _vp, _u32, _vp, _vp, _sz]),
     "rs_sort_pairs_segmented_ex": (_int, [_vp, _vp, _sz, _vp, _u32, _vp, _vp, _sz]),
+    "rs_sort_typed_ex": (_int, [_vp, _vp, _sz, _int, _vp, _vp, _sz]),
+    "rs_sort_segmented_typed_ex": (_int, [_vp, _vp, _sz, _vp, _u32, _int, _vp, _vp, _sz]),
     "rs_workspace_bytes": (_sz, [_sz, _int, _u32]),
     "rs_stream_status": (_int, [_vp]),
     "rs_status_string": (ctypes.c_char_p, [_int]),
@@ -198,6 +200,44 @@ def sort_pairs_segmented_ex(keys, vals, offsets, workspace, stream=None) -> None
                                             keys.numel(), op, ns, _stream_handle(stream),
                                             workspace.data_ptr(), workspace.numel()),
            "rs_sort_pairs_segmented_ex")
+
+
+KEY_TYPES = {"u32": 0, "i32": 1, "f32": 2}
+
+
+def sort_typed_ex(keys, vals, key_type: str, workspace, stream=None) -> None:
+    """Enqueue an in-place sort of keys read as ``key_type`` ("u32", "i32" or
+    "f32"; the tensor holds the 32-bit patterns), values optional."""
+    if vals is not None and vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    _check(lib().rs_sort_typed_ex(_dev_ptr(keys, "keys"),
+                                  None if vals is None else _dev_ptr(vals, "vals"), keys.numel(),
+                                  KEY_TYPES[key_type], _stream_handle(stream),
+                                  workspace.data_ptr(), workspace.numel()), "rs_sort_typed_ex")
+
+
+def sort_segmented_typed_ex(keys, vals, offsets, key_type: str, workspace, stream=None) -> None:
+    """Enqueue the typed sort of every segment [offsets[s], offsets[s+1])."""
+    if vals is not None and vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    op, ns = _segments(offsets)
+    _check(lib().rs_sort_segmented_typed_ex(_dev_ptr(keys, "keys"),
+                                            None if vals is None else _dev_ptr(vals, "vals"),
+                                            keys.numel(), op, ns, KEY_TYPES[key_type],
+                                            _stream_handle(stream), workspace.data_ptr(),
+                                            workspace.numel()), "rs_sort_segmented_typed_ex")
+
+
+def sort_typed(keys, vals=None, key_type: str = "f32", offsets=None, stream=None) -> None:
+    """Synchronous typed sort (whole array, or per segment with ``offsets``)
+    with a workspace allocated for the call; raises on any device error."""
+    nseg = 0 if offsets is None else max(offsets.numel() - 1, 0)
+    ws = alloc_workspace(keys.numel(), vals is not None, nseg, device=keys.device)
+    if offsets is None:
+        sort_typed_ex(keys, vals, key_type, ws, stream)
+    else:
+        sort_segmented_typed_ex(keys, vals, offsets, key_type, ws, stream)
+    check_stream(stream)
 
 
 def stream_status(stream=None) -> int:
