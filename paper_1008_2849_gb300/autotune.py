@@ -6,7 +6,9 @@ captured CUDA graphs (rs_graph_*) of a representative synthetic workload
 under every candidate setting and keeps the fastest:
 
 * whole arrays: the tile shape of the scatter passes, for key-value and for
-  keys-only sorts; for arrays up to 8192 items, which take the one-warp sort
+  keys-only sorts; up to 2^21 items, the MSD-first order of Alg. 2 (one pass
+  by the top digit, then on-chip bucket sorts) or the four LSD passes; for
+  arrays up to 8192 items, which take the one-warp sort
   (up to 512 items) and the one-CTA sort, and at which digit width;
 * segmented batches: the tile shape of the segmented scatter passes and the
   largest segment sorted by the one-CTA sort (4096 or 8192); for batches of
@@ -31,6 +33,7 @@ import numpy as np
 
 # Representative item counts per size class (whole arrays).
 CLASS_SIZES = {1: 1 << 16, 2: 1 << 20, 3: 1 << 24, 4: 1 << 27}
+MSD_MAX_ITEMS = 256 * 8192  # largest whole array the MSD-first order is tried for
 
 
 def _time_graph(rs, torch, graph, restore, reps):
@@ -61,6 +64,8 @@ def tune_whole(rs, torch, inputs, reps=3, quick=False):
         v = torch.arange(n, dtype=torch.int32, device="cuda")
         kb, vb = torch.empty_like(k), torch.empty_like(v)
         best = {}
+        saved = {kn: rs.tune_get_class(cls, kn) for kn in ("tile_pairs", "tile_keys", "msd")}
+        rs.tune_set_class(cls, "msd", 0)  # shapes are timed on the four LSD passes
         for pairs in (True, False):
             knob = "tile_pairs" if pairs else "tile_keys"
             old = rs.tune_get_class(cls, knob)
@@ -77,6 +82,28 @@ def tune_whole(rs, torch, inputs, reps=3, quick=False):
             rs.tune_set_class(cls, knob, old)
             best[knob] = min(res, key=res.get)
             best[knob + "_ms"] = res
+            rs.tune_set_class(cls, knob, best[knob])
+        if n <= MSD_MAX_ITEMS:
+            # MSD-first order (one top-digit pass + on-chip bucket sorts) or
+            # the four LSD passes, with the chosen shapes; pairs + keys time.
+            old_msd = rs.tune_get_class(cls, "msd")
+            res = {}
+            for msd in (0, 1):
+                rs.tune_set_class(cls, "msd", msd)
+                tot = 0.0
+                for pairs in (True, False):
+                    def restore():
+                        kb.copy_(k)
+                        vb.copy_(v)
+                    g = rs.Graph(kb, vb if pairs else None)
+                    tot += _time_graph(rs, torch, g, restore, reps)
+                    g.close()
+                res[msd] = tot
+            rs.tune_set_class(cls, "msd", old_msd)
+            best["msd"] = min(res, key=res.get)
+            best["msd_ms"] = res
+        for knob in ("tile_pairs", "tile_keys", "msd"):
+            rs.tune_set_class(cls, knob, saved[knob])
         out[str(cls)] = best
         del k, v, kb, vb
         torch.cuda.empty_cache()
@@ -183,7 +210,8 @@ def apply(table: dict) -> None:
     """Set the library's per-class knobs from a table made by this module."""
     from paper_1008_2849_gb300 import rs
     for cls, knobs in table.get("classes", {}).items():
-        for name in ("tile_pairs", "tile_keys", "tile_seg", "small_max", "warp_max", "small_bits"):
+        for name in ("tile_pairs", "tile_keys", "tile_seg", "small_max", "warp_max", "small_bits",
+                     "msd"):
             if name in knobs:
                 rs.tune_set_class(int(cls), name, int(knobs[name]))
 

@@ -2,9 +2,13 @@
 
     python -m paper_1008_2849_gb300.bench_configs [--steps K] [--warmup W]
 
-1. Keys only, 2^20 uniform uint32 keys (seed 1), four 8-bit passes: device
-   time of one rs_sort_keys_ex (median of K), so a latency.  The array is
-   4 MiB and stays in L2 between steps: this case is not an HBM roofline case.
+1. Keys only, 2^20 uniform uint32 keys (seed 1), four 8-bit LSD passes:
+   device time of one rs_sort_keys_ex (median of K), so a latency.  The array
+   is 4 MiB and stays in L2 between steps: this case is not an HBM roofline
+   case.  The same input is also timed in the MSD-first order of Alg. 2, and
+   uniform pairs of 2^14..2^21 items in both orders; each also as the replay
+   of a captured graph (rs_graph_launch), which removes the host's launch
+   overhead from the device timeline.
 2. Distribution sweep at 2^27 pairs (value = index; seeds 3, 4, ...):
    uniform; AND of 2, 3 and 4 uniform words; 256 distinct values; all keys
    equal; sorted; reverse sorted; low 16 bits only.  Each step sorts a fresh
@@ -58,16 +62,56 @@ def main(argv=None) -> int:
     stream = torch.cuda.current_stream()
     out = {"metric": "sort throughput and latency per configuration", "unit": "pairs/s"}
 
-    # 1. keys only, 2^20
+    # 1. keys only, 2^20: the four LSD passes (as the configuration states),
+    # and the MSD-first order of Alg. 2 on the same input (same result).
     n = 1 << 20
     k = torch.from_numpy(inputs.keys("uniform", n, seed=1).view(np.int32)).cuda()
     kb = torch.empty_like(k)
     ws = rs.alloc_workspace(n, False)
-    ms = _timed(torch, stream, lambda: rs.sort_keys_ex(kb, ws, stream), lambda: kb.copy_(k),
-                a.steps, a.warmup)
-    rs.check_stream()
-    out["keys_2^20_uniform_seed1"] = {"ms": ms, "keys_per_s": n / (ms / 1e3)}
+    cls = rs.size_class(n)
+    old_msd = rs.tune_get_class(cls, "msd")
+    for msd, name in ((0, "keys_2^20_uniform_seed1"), (1, "keys_2^20_uniform_seed1_msd_first")):
+        rs.tune_set_class(cls, "msd", msd)
+        ms = _timed(torch, stream, lambda: rs.sort_keys_ex(kb, ws, stream), lambda: kb.copy_(k),
+                    a.steps, a.warmup)
+        g = rs.Graph(kb, None, None, ws)
+        ms_graph = _timed(torch, stream, lambda: g.launch(stream), lambda: kb.copy_(k), a.steps,
+                          a.warmup)
+        g.close()
+        rs.check_stream()
+        out[name] = {"ms": ms, "keys_per_s": n / (ms / 1e3), "graph_replay_ms": ms_graph}
+    rs.tune_set_class(cls, "msd", old_msd)
     del k, kb, ws
+
+    # Mid-size pairs: LSD passes vs MSD-first order.
+    mid = {}
+    for lg in (14, 16, 18, 20, 21):
+        n = 1 << lg
+        k = torch.from_numpy(inputs.keys("uniform", n, seed=40 + lg).view(np.int32)).cuda()
+        v = torch.arange(n, dtype=torch.int32, device="cuda")
+        kb, vb = torch.empty_like(k), torch.empty_like(v)
+        ws = rs.alloc_workspace(n, True)
+        cls = rs.size_class(n)
+        old_msd = rs.tune_get_class(cls, "msd")
+        row = {}
+        for msd in (0, 1):
+            rs.tune_set_class(cls, "msd", msd)
+
+            def restore():
+                kb.copy_(k)
+                vb.copy_(v)
+            ms = _timed(torch, stream, lambda: rs.sort_pairs_ex(kb, vb, ws, stream), restore,
+                        a.steps, a.warmup)
+            g = rs.Graph(kb, vb, None, ws)
+            ms_graph = _timed(torch, stream, lambda: g.launch(stream), restore, a.steps, a.warmup)
+            g.close()
+            rs.check_stream()
+            row["msd_first" if msd else "lsd"] = {"ms": ms, "pairs_per_s": n / (ms / 1e3),
+                                                  "graph_replay_ms": ms_graph}
+        rs.tune_set_class(cls, "msd", old_msd)
+        mid["2^%d" % lg] = row
+        del k, v, kb, vb, ws
+    out["pairs_mid_sizes_lsd_vs_msd_first"] = mid
 
     # 2. distribution sweep, 2^27 pairs
     n = 1 << 27

@@ -4,6 +4,8 @@
 // global loads/stores, and the error bits kernels record instead of faulting.
 #pragma once
 
+#include <cstddef>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -31,18 +33,25 @@ constexpr uint32_t DIR_B_TO_A = 2; // alternate buffers -> caller's arrays
 
 // Per-call control block, zeroed by one cudaMemsetAsync at the start of a
 // call.  Lives at the start of the workspace.
+// Plan slots: the LSD passes 0..3, and MSD_SLOT for the most-significant-digit
+// pass of the MSD-first order (Alg. 2), which runs before the passes 0..3 are
+// reached and, when the plan chooses it, makes them all DIR_SKIP.
+constexpr uint32_t MSD_SLOT = PASSES;
+constexpr uint32_t PLAN_SLOTS = PASSES + 1;
+
 struct Ctrl {
     uint32_t err;                  // error bits of this call
-    uint32_t tile_ctr[PASSES];     // dynamic tile ids, one counter per pass
-    uint32_t dir[PASSES];          // pass plan
+    uint32_t tile_ctr[PLAN_SLOTS]; // dynamic tile ids, one counter per plan slot
+    uint32_t dir[PLAN_SLOTS];      // pass plan
     uint32_t seg_tiles;            // segmented sorts: tiles of the large segments
-    uint32_t small_count;          // segmented sorts: number of small segments
+    uint32_t small_count;          // segmented sorts (and MSD buckets): one-CTA segments
     uint32_t large_count;          // segmented sorts: number of large segments
-    uint32_t tiny_count;           // segmented sorts: number of tiny segments
-    uint32_t pad[3];               // keep hist 64-byte aligned
+    uint32_t tiny_count;           // segmented sorts (and MSD buckets): one-warp segments
+    uint32_t pad[1];               // keep hist 64-byte aligned
     uint32_t hist[PASSES][RADIX];  // digit histograms (H)
     uint32_t gofs[PASSES][RADIX];  // first output slot of every bucket (G)
 };
+static_assert(offsetof(Ctrl, hist) % 64 == 0, "histograms 64-byte aligned");
 
 // Key types.  A typed key is mapped onto an unsigned word with the same
 // order before its digits are read, and mapped back when it is stored:

@@ -170,13 +170,28 @@ k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
 // number of executed passes is kept even (one trivial pass is run if needed)
 // so that the ping-pong between the caller's arrays and the alternate
 // buffers ends in the caller's arrays.
+//
+// MSD-first order (Alg. 2, "reverse sorting"), when msd_allowed: if digit 3
+// is not trivial and no digit-3 bucket holds more than bucket_cap keys, the
+// plan runs one pass by digit 3 (plan slot MSD_SLOT, caller's arrays ->
+// alternate buffers) and skips passes 0..3; every bucket is then sorted on
+// chip from the alternate buffers back into the caller's arrays (its digit 3
+// is constant, so that pass is trivial there).  msd_off[b] is bucket b's
+// first slot (msd_off[256] = n); non-empty buckets of at most warp_max keys
+// are listed in tiny_list (one-warp sort), larger ones in small_list
+// (one-CTA sort).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_plan(Ctrl* __restrict__ ctrl, uint32_t n) {
+__global__ void __launch_bounds__(1024)
+k_plan(Ctrl* __restrict__ ctrl, uint32_t n, uint32_t msd_allowed, uint32_t warp_max,
+       uint32_t bucket_cap, uint32_t* __restrict__ msd_off, uint32_t* __restrict__ tiny_list,
+       uint32_t* __restrict__ small_list) {
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_trivial[PASSES];
+    __shared__ uint32_t s_big;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = tid >> 8, b = tid & (RADIX - 1);
     if (tid < PASSES) s_trivial[tid] = 0;
+    if (tid == 0) s_big = 0;
     const uint32_t h = ctrl->hist[p][b];
     uint32_t x = h;
 #pragma unroll
@@ -188,10 +203,27 @@ __global__ void __launch_bounds__(1024) k_plan(Ctrl* __restrict__ ctrl, uint32_t
     __syncthreads();
     uint32_t off = 0;
     for (uint32_t w = p * (RADIX / 32); w < warp; ++w) off += s_warp[w];
-    ctrl->gofs[p][b] = off + x - h;
+    const uint32_t first = off + x - h;
+    ctrl->gofs[p][b] = first;
     if (h == n) s_trivial[p] = 1;
+    if (p == PASSES - 1 && h > bucket_cap) s_big = 1;
     __syncthreads();
-    if (tid == 0) {
+    const bool msd = msd_allowed && !s_trivial[PASSES - 1] && !s_big;
+    if (msd && p == PASSES - 1) {
+        msd_off[b] = first;
+        if (b == RADIX - 1) msd_off[RADIX] = n;
+        if (h > 0) {
+            if (h <= warp_max)
+                tiny_list[atomicAdd(&ctrl->tiny_count, 1u)] = b;
+            else
+                small_list[atomicAdd(&ctrl->small_count, 1u)] = b;
+        }
+    }
+    if (tid == 0 && msd) {
+        for (uint32_t q = 0; q < PASSES; ++q) ctrl->dir[q] = DIR_SKIP;
+        ctrl->dir[MSD_SLOT] = DIR_A_TO_B;
+    } else if (tid == 0) {
+        ctrl->dir[MSD_SLOT] = DIR_SKIP;
         uint32_t trivial[PASSES], executed = 0;
         for (uint32_t q = 0; q < PASSES; ++q) {
             trivial[q] = s_trivial[q];

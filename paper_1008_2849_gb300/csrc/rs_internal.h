@@ -69,7 +69,11 @@ struct ClassKnobs {
     int small_max;
     int warp_max;
     int small_bits;
+    int msd;        // 1: whole arrays up to kMsdMaxItems may take the MSD-first order
 };
+// Largest whole array the MSD-first order is tried for: 256 buckets of at
+// most the one-CTA sort's capacity.
+constexpr uint32_t kMsdMaxItems = 256u * 8192u;
 // Size classes by item count (whole array; for a segmented sort the average
 // segment): <= 2^13, <= 2^16, <= 2^20, <= 2^24, <= 2^28, larger.
 constexpr int NUM_SIZE_CLASSES = 6;
@@ -98,7 +102,7 @@ rs_status device_info(DeviceInfo* out);
 
 // Workspace layout of an unsegmented sort of n items.
 struct Layout {
-    size_t ctrl, status0, status1, alt_keys, alt_vals, total;
+    size_t ctrl, status0, status1, alt_keys, alt_vals, msd_off, msd_tiny, msd_small, total;
     uint32_t tiles;          // tiles of the smallest tile shape (status sizing)
     bool wide_status;        // 64-bit status words (n >= 2^30)
 };
@@ -124,22 +128,26 @@ struct SegView {
 // Scatter-pass launchers, one per value flavour (separate translation units);
 // seg == nullptr for the unsegmented sort.
 // key_type: KEY_U32, KEY_I32 or KEY_F32 (rs_device.cuh).
+// slot: the plan entry of the launch (the pass, or MSD_SLOT).
 rs_status launch_onesweep_keys(int cfg, bool wide, uint32_t* ka, uint32_t* kb, uint32_t n,
-                               uint32_t pass, Ctrl* ctrl, uint32_t* sticky, void* status,
-                               void* status_clear, const SegView* seg, uint32_t key_type,
-                               cudaStream_t stream);
+                               uint32_t pass, uint32_t slot, Ctrl* ctrl, uint32_t* sticky,
+                               void* status, void* status_clear, const SegView* seg,
+                               uint32_t key_type, cudaStream_t stream);
 rs_status launch_onesweep_pairs(int cfg, bool wide, uint32_t* ka, uint32_t* va, uint32_t* kb,
-                                uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
-                                uint32_t* sticky, void* status, void* status_clear,
+                                uint32_t* vb, uint32_t n, uint32_t pass, uint32_t slot,
+                                Ctrl* ctrl, uint32_t* sticky, void* status, void* status_clear,
                                 const SegView* seg, uint32_t key_type, cudaStream_t stream);
 
 // One-CTA sort in shared memory: of every small segment listed by the
 // segmented planner (off != nullptr; none longer than max_items), or of the
 // single array [0, single_n) with single_n <= max_items <= small_sort_capacity().
 // bits: digit width, 4 or 8.
+// src_keys / src_vals (default: keys / vals, in place) is where items are read.
 rs_status launch_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
                             const uint32_t* small_list, const Ctrl* ctrl, uint32_t single_n,
-                            uint32_t max_items, int bits, uint32_t key_type, cudaStream_t stream);
+                            uint32_t max_items, int bits, uint32_t key_type, cudaStream_t stream,
+                            const uint32_t* src_keys = nullptr,
+                            const uint32_t* src_vals = nullptr);
 uint32_t small_sort_capacity();
 
 // One-warp sort in shared memory: of every tiny segment listed by the
@@ -147,7 +155,8 @@ uint32_t small_sort_capacity();
 // with single_n <= warp_sort_capacity().  bits: digit width, 4 or 8.
 rs_status launch_warp_sort(uint32_t* keys, uint32_t* vals, const uint32_t* off,
                            const uint32_t* tiny_list, const Ctrl* ctrl, uint32_t single_n,
-                           int bits, uint32_t key_type, cudaStream_t stream);
+                           int bits, uint32_t key_type, cudaStream_t stream,
+                           const uint32_t* src_keys = nullptr, const uint32_t* src_vals = nullptr);
 uint32_t warp_sort_capacity();
 
 // Workspace layout of a segmented sort of n items in num_segments segments.

@@ -38,7 +38,9 @@ struct OnesweepSmem {
 
 // ---------------------------------------------------------------------------
 // k_onesweep: one stable counting-sort pass by digit `pass` over tiles of
-// TILE = THREADS * ITEMS items, run by a persistent grid.
+// TILE = THREADS * ITEMS items, run by a persistent grid.  `slot` names the
+// plan entry (ctrl->dir, ctrl->tile_ctr) of the launch: the pass itself, or
+// MSD_SLOT for the first pass of the MSD-first order.
 //
 // Tile flow inside a CTA (tile ids come from an atomic counter, in increasing
 // order per CTA): while tile i is ranked, the keys of tile i+1 are already
@@ -96,7 +98,7 @@ template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WI
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
 k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
            uint32_t* __restrict__ kb, uint32_t* __restrict__ vb,
-           uint32_t n, uint32_t pass, uint32_t num_tiles, Ctrl* __restrict__ ctrl,
+           uint32_t n, uint32_t pass, uint32_t slot, uint32_t num_tiles, Ctrl* __restrict__ ctrl,
            uint32_t* __restrict__ sticky, S* __restrict__ status, S* __restrict__ status_clear,
            uint32_t clear_words, uint32_t spin_limit, uint32_t debug,
            const uint4* __restrict__ tile_geo, const uint32_t* __restrict__ seg_gofs,
@@ -143,7 +145,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         if (ld_relaxed(&ctrl->err) != 0) return;  // malformed segment table: no work
         num_tiles = ctrl->seg_tiles;
     }
-    const uint32_t dir = ctrl->dir[pass];
+    const uint32_t dir = ctrl->dir[slot];
     if (dir == DIR_SKIP) {
         // No tiles in this pass: clear the whole next status array here.
         if (status_clear != nullptr)
@@ -183,7 +185,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     if (tid == 0) {
         for (int b = 0; b < 3; ++b) mbar_init(&s_bar[b], 1);
         fence_mbar_init();
-        s_ids[0] = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+        s_ids[0] = atomicAdd(&ctrl->tile_ctr[slot], 1u);
         s_geo[0] = load_geo(s_ids[0]);
         s_flag = 0;
         s_err_seen = 0;
@@ -304,7 +306,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     __syncthreads();
     if (tid < RADIX) prep_tile(s_ids[0], s_geo[0].z);
     if (tid == 0) {
-        s_ids[1] = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+        s_ids[1] = atomicAdd(&ctrl->tile_ctr[slot], 1u);
         s_geo[1] = load_geo(s_ids[1]);
     }
     __syncthreads();
@@ -442,7 +444,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
                 // This CTA waits on no other CTA from here until the counts of
                 // the tile taken now are published: taking it cannot stall
                 // anyone.
-                next_id = atomicAdd(&ctrl->tile_ctr[pass], 1u);
+                next_id = atomicAdd(&ctrl->tile_ctr[slot], 1u);
                 next_geo = load_geo(next_id);
             }
         }

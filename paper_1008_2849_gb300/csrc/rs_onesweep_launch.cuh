@@ -19,7 +19,8 @@ RS_TILE_SHAPES(RS_SHAPE_STRUCT)
 template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S, bool SEG,
           bool TYPED>
 static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
-                                       uint32_t n, uint32_t pass, Ctrl* ctrl, uint32_t* sticky,
+                                       uint32_t n, uint32_t pass, uint32_t slot, Ctrl* ctrl,
+                                       uint32_t* sticky,
                                        void* status, void* status_clear, const SegView& seg,
                                        uint32_t key_type, cudaStream_t stream) {
     using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
@@ -48,7 +49,7 @@ static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb,
     if (grid > tiles) grid = tiles;
     if (grid == 0) return RS_OK;
     note_launch_begin(SEG ? KK_SEG_ONESWEEP : KK_ONESWEEP, stream);
-    kern<<<grid, THREADS, L::BYTES, stream>>>(ka, va, kb, vb, n, pass, tiles, ctrl, sticky,
+    kern<<<grid, THREADS, L::BYTES, stream>>>(ka, va, kb, vb, n, pass, slot, tiles, ctrl, sticky,
                                               static_cast<S*>(status), static_cast<S*>(status_clear),
                                               tiles * RADIX, knobs().spin_limit, knobs().debug,
                                               seg.tile_geo, seg.gofs, key_type);
@@ -58,21 +59,22 @@ static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb,
 
 template <bool PAIRS, typename S, bool SEG>
 static rs_status launch_onesweep_variant(int cfg, uint32_t* ka, uint32_t* va, uint32_t* kb,
-                                         uint32_t* vb, uint32_t n, uint32_t pass, Ctrl* ctrl,
+                                         uint32_t* vb, uint32_t n, uint32_t pass, uint32_t slot,
+                                         Ctrl* ctrl,
                                          uint32_t* sticky, void* status, void* status_clear,
                                          const SegView& seg, uint32_t key_type,
                                          cudaStream_t stream) {
     if (key_type != KEY_U32) {
         using T = TileShape<kTypedShape>;
         return launch_onesweep_shape<T::threads, T::items, T::min_blocks, T::window, PAIRS, S, SEG,
-                                     true>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
+                                     true>(ka, va, kb, vb, n, pass, slot, ctrl, sticky, status,
                                            status_clear, seg, key_type, stream);
     }
     switch (cfg) {
 #define RS_CASE(I, T, J, B, W)                                                                    \
     case I:                                                                                       \
         return launch_onesweep_shape<T, J, B, W, PAIRS, S, SEG, false>(                           \
-            ka, va, kb, vb, n, pass, ctrl, sticky, status, status_clear, seg, KEY_U32, stream);
+            ka, va, kb, vb, n, pass, slot, ctrl, sticky, status, status_clear, seg, KEY_U32, stream);
         RS_TILE_SHAPES(RS_CASE)
 #undef RS_CASE
     default: return RS_ERR_INVALID_ARG;

@@ -114,10 +114,10 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
         view.gofs = gofs;
         void* cur = status[p & 1];
         void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;
-        st = pairs ? launch_onesweep_pairs(cfg, false, keys, vals, alt_k, alt_v, n, p, ctrl,
+        st = pairs ? launch_onesweep_pairs(cfg, false, keys, vals, alt_k, alt_v, n, p, p, ctrl,
                                            di.sticky, cur, next, &view, key_type, stream)
-                   : launch_onesweep_keys(cfg, false, keys, alt_k, n, p, ctrl, di.sticky, cur, next,
-                                          &view, key_type, stream);
+                   : launch_onesweep_keys(cfg, false, keys, alt_k, n, p, p, ctrl, di.sticky, cur,
+                                          next, &view, key_type, stream);
         if (st != RS_OK) return st;
     }
     return RS_OK;

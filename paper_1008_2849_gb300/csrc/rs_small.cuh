@@ -6,7 +6,9 @@
 // scatter passes) or 4 bits (eight passes, 16 buckets) -- which is faster
 // depends on the array size, and the autotuner picks it per size class.
 // Either width gives the same stable order.  Typed keys (key_type) are mapped
-// onto their ordered words when read and back when written.
+// onto their ordered words when read and back when written.  An array is read
+// from src_keys / src_vals and written to keys / vals at the same offsets (the
+// same arrays for an in-place sort; the other buffer after an MSD pass).
 #pragma once
 
 #include "rs_device.cuh"
@@ -46,7 +48,7 @@ struct WarpSortSmem {
 // ---------------------------------------------------------------------------
 template <int ITEMS, int BITS, bool PAIRS>
 __global__ void __launch_bounds__(WARP_SORT_THREADS)
-k_warp_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+k_warp_sort(uint32_t* keys, uint32_t* vals, const uint32_t* src_keys, const uint32_t* src_vals,
             const uint32_t* __restrict__ off, const uint32_t* __restrict__ list,
             const Ctrl* __restrict__ ctrl, uint32_t single_n, uint32_t key_type) {
     using L = WarpSortSmem<ITEMS, BITS, PAIRS>;
@@ -76,8 +78,8 @@ k_warp_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
             m = off[s + 1] - lo;
         }
         for (uint32_t i = lane; i < m; i += 32) {
-            s_k[i] = key_to_ordered(keys[lo + i], key_type);
-            if (PAIRS) s_v[i] = vals[lo + i];
+            s_k[i] = key_to_ordered(src_keys[lo + i], key_type);
+            if (PAIRS) s_v[i] = src_vals[lo + i];
         }
         uint32_t cur = 0;
         for (uint32_t p = 0; p < NPASS; ++p) {
@@ -162,7 +164,7 @@ k_warp_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
 // ---------------------------------------------------------------------------
 template <int THREADS, int ITEMS, int BITS, bool PAIRS>
 __global__ void __launch_bounds__(THREADS)
-k_small_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+k_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* src_keys, const uint32_t* src_vals,
              const uint32_t* __restrict__ off, const uint32_t* __restrict__ small_list,
              const Ctrl* __restrict__ ctrl, uint32_t single_n, uint32_t key_type) {
     constexpr uint32_t NB = 1u << BITS;
@@ -196,8 +198,8 @@ k_small_sort(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
             m = off[s + 1] - lo;
         }
         for (uint32_t i = tid; i < m; i += THREADS) {
-            s_k[i] = key_to_ordered(keys[lo + i], key_type);
-            if (PAIRS) s_v[i] = vals[lo + i];
+            s_k[i] = key_to_ordered(src_keys[lo + i], key_type);
+            if (PAIRS) s_v[i] = src_vals[lo + i];
         }
         __syncthreads();
         uint32_t cur = 0;

@@ -37,6 +37,12 @@ Layout layout_for(size_t n, bool pairs) {
     off = align_up(off + n * sizeof(uint32_t), 256);
     L.alt_vals = off;
     if (pairs) off = align_up(off + n * sizeof(uint32_t), 256);
+    L.msd_off = off;  // MSD-first order: bucket offsets and bucket lists
+    off = align_up(off + (RADIX + 1) * sizeof(uint32_t), 256);
+    L.msd_tiny = off;
+    off = align_up(off + RADIX * sizeof(uint32_t), 256);
+    L.msd_small = off;
+    off = align_up(off + RADIX * sizeof(uint32_t), 256);
     L.total = off;
     return L;
 }
@@ -117,21 +123,51 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     uint32_t* alt_k = reinterpret_cast<uint32_t*>(ws + L.alt_keys);
     uint32_t* alt_v = pairs ? reinterpret_cast<uint32_t*>(ws + L.alt_vals) : nullptr;
 
+    // MSD-first order (Alg. 2): tried for unsigned arrays that can split into
+    // 256 buckets the one-CTA sort takes; the plan decides on the device
+    // from the digit-3 histogram, so the launch sequence stays fixed.
+    const bool msd = ck.msd != 0 && key_type == KEY_U32 && n <= kMsdMaxItems;
+    uint32_t* msd_off = reinterpret_cast<uint32_t*>(ws + L.msd_off);
+    uint32_t* msd_tiny = reinterpret_cast<uint32_t*>(ws + L.msd_tiny);
+    uint32_t* msd_small = reinterpret_cast<uint32_t*>(ws + L.msd_small);
+    const uint32_t warp_max =
+        (uint32_t)ck.warp_max < warp_sort_capacity() ? (uint32_t)ck.warp_max : warp_sort_capacity();
+
     if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return RS_ERR_CUDA;
     st = launch_hist(keys, n, &ctrl->hist[0][0], status[0], status_bytes, key_type, stream);
     if (st != RS_OK) return st;
     note_launch_begin(KK_PLAN, stream);
-    k_plan<<<1, 1024, 0, stream>>>(ctrl, n);
+    k_plan<<<1, 1024, 0, stream>>>(ctrl, n, msd ? 1u : 0u, warp_max, small_sort_capacity(),
+                                   msd_off, msd_tiny, msd_small);
     note_launch_end(KK_PLAN, stream);
     if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
 
     const int cfg = pairs ? ck.tile_pairs : ck.tile_keys;
+    if (msd) {
+        // One pass by digit 3 into the alternate buffers (skipped unless the
+        // plan chose this order), then every bucket on chip back into the
+        // caller's arrays.
+        st = pairs ? launch_onesweep_pairs(cfg, false, keys, vals, alt_k, alt_v, n, PASSES - 1,
+                                           MSD_SLOT, ctrl, di.sticky, status[0], nullptr, nullptr,
+                                           KEY_U32, stream)
+                   : launch_onesweep_keys(cfg, false, keys, alt_k, n, PASSES - 1, MSD_SLOT, ctrl,
+                                          di.sticky, status[0], nullptr, nullptr, KEY_U32, stream);
+        if (st != RS_OK) return st;
+        if (warp_max > 0) {
+            st = launch_warp_sort(keys, vals, msd_off, msd_tiny, ctrl, 0, ck.small_bits, KEY_U32,
+                                  stream, alt_k, alt_v);
+            if (st != RS_OK) return st;
+        }
+        st = launch_small_sort(keys, vals, msd_off, msd_small, ctrl, 0, small_sort_capacity(),
+                               ck.small_bits, KEY_U32, stream, alt_k, alt_v);
+        if (st != RS_OK) return st;
+    }
     for (uint32_t p = 0; p < PASSES; ++p) {
         void* cur = status[p & 1];
         void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;
-        st = pairs ? launch_onesweep_pairs(cfg, L.wide_status, keys, vals, alt_k, alt_v, n, p, ctrl,
-                                           di.sticky, cur, next, nullptr, key_type, stream)
-                   : launch_onesweep_keys(cfg, L.wide_status, keys, alt_k, n, p, ctrl, di.sticky,
+        st = pairs ? launch_onesweep_pairs(cfg, L.wide_status, keys, vals, alt_k, alt_v, n, p, p,
+                                           ctrl, di.sticky, cur, next, nullptr, key_type, stream)
+                   : launch_onesweep_keys(cfg, L.wide_status, keys, alt_k, n, p, p, ctrl, di.sticky,
                                           cur, next, nullptr, key_type, stream);
         if (st != RS_OK) return st;
     }

@@ -51,12 +51,20 @@ def test_keys_edge_sizes(rs, n):
 
 
 def test_keys_2pow20_uniform_seed1(rs):
-    """2^20 uniform keys, seed 1, keys only, four 8-bit passes."""
+    """2^20 uniform keys, seed 1, keys only, four 8-bit LSD passes (the MSD-
+    first order off, as the configuration states), and with it on."""
     n = 1 << 20
     k = inputs.keys("uniform", n, seed=1)
-    kd = to_dev(k)
-    rs.sort_keys(kd)
-    assert np.array_equal(to_host(kd), oracle.sort_keys(k))
+    cls = rs.size_class(n)
+    old = rs.tune_get_class(cls, "msd")
+    try:
+        for msd in (0, 1):
+            rs.tune_set_class(cls, "msd", msd)
+            kd = to_dev(k)
+            rs.sort_keys(kd)
+            assert np.array_equal(to_host(kd), oracle.sort_keys(k))
+    finally:
+        rs.tune_set_class(cls, "msd", old)
 
 
 def test_pairs_2pow28_uniform(rs):
@@ -214,3 +222,68 @@ def test_wide_status_2pow30_plus(rs):
     seen = torch.zeros(n, dtype=torch.bool, device="cuda")
     seen[vals.long()] = True
     assert bool(seen.all())
+
+
+def _plan_slots_used(ws):
+    """Tiles taken per plan slot by the last sort that used workspace `ws`:
+    the control block sits at the start of the workspace (err, then the
+    five tile counters: LSD passes 0..3 and the MSD pass)."""
+    head = ws[:24].cpu().numpy().view(np.uint32)
+    return head[1:6].tolist()
+
+
+def _msd_keys(kind, n, seed):
+    if kind == "top_few":          # top byte in 0..3: four large buckets
+        k = inputs.keys("uniform", n, seed) & np.uint32(0x03FFFFFF)
+    elif kind == "lone_bucket":    # plus one key alone in bucket 255 (a size-1 bucket)
+        k = inputs.keys("uniform", n, seed) & np.uint32(0x03FFFFFF)
+        k[n // 2] = 0xFF000001
+    else:
+        k = inputs.keys(kind, n, seed)
+    return k
+
+
+@pytest.mark.parametrize("kind,n,taken", [
+    ("uniform", 8193, True), ("uniform", 65_537, True), ("uniform", (1 << 18) + 5, True),
+    ("uniform", 1 << 20, True), ("uniform", (1 << 21) - 3, None),
+    ("top_few", 20_000, True), ("lone_bucket", 9_000, True),
+    ("low16", 100_000, False),        # top digit constant: the MSD pass would do nothing
+    ("and4", 1 << 20, False),         # top-digit bucket 0 far above 8192 keys
+])
+def test_msd_first_order(rs, kind, n, taken):
+    """Whole arrays that may take the MSD-first order of Alg. 2 (one pass by
+    the top digit, then every bucket sorted on chip): the result equals the
+    oracle's LSD sort whichever order the plan chose, with the MSD order on
+    and off, pairs and keys; where the choice is fixed by the data, the plan
+    is checked to have made it."""
+    import torch
+    k = _msd_keys(kind, n, seed=300 + n % 89)
+    v = inputs.index_values(n)
+    ko, vo = oracle_sort(k, v)
+    cls = rs.size_class(n)
+    old = rs.tune_get_class(cls, "msd")
+    try:
+        for msd in (1, 0):
+            rs.tune_set_class(cls, "msd", msd)
+            for pairs in (True, False):
+                kd, vd = to_dev(k), to_dev(v)
+                ws = rs.alloc_workspace(n, pairs)
+                if pairs:
+                    rs.sort_pairs_ex(kd, vd, ws)
+                else:
+                    rs.sort_keys_ex(kd, ws)
+                rs.check_stream()
+                assert np.array_equal(to_host(kd), ko), (kind, n, msd, pairs)
+                if pairs:
+                    assert np.array_equal(to_host(vd), vo), (kind, n, msd, pairs)
+                tiles = _plan_slots_used(ws)
+                used_msd = tiles[4] > 0
+                if msd == 0 or n > (1 << 21):
+                    assert not used_msd
+                elif taken is not None:
+                    assert used_msd == taken, (kind, n, tiles)
+                if used_msd:
+                    assert tiles[:4] == [0, 0, 0, 0]
+                torch.cuda.synchronize()
+    finally:
+        rs.tune_set_class(cls, "msd", old)
