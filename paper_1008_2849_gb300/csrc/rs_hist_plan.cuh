@@ -31,7 +31,9 @@ constexpr int HIST_LEADER = 1;
 constexpr int HIST_MATCH = 2;
 constexpr int HIST_COLUMNS = 3;  // k_hist4_cols
 
-template <int THREADS, int MODE>
+// TYPED: keys are mapped onto their ordered words (key_type) before counting;
+// unsigned keys use the instances without the map.
+template <int THREADS, int MODE, bool TYPED>
 __global__ void __launch_bounds__(THREADS)
 k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
         uint4* __restrict__ clear, uint32_t clear_vec4, uint32_t key_type) {
@@ -52,7 +54,7 @@ k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hi
     const uint4* __restrict__ body = reinterpret_cast<const uint4*>(keys + head);
 
     auto count_key = [&](uint32_t key, bool ok) {
-        key = key_to_ordered(key, key_type);
+        if (TYPED) key = key_to_ordered(key, key_type);
 #pragma unroll
         for (uint32_t p = 0; p < PASSES; ++p) {
             const uint32_t d = (key >> (p * RADIX_BITS)) & (RADIX - 1);
@@ -90,7 +92,7 @@ k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hi
         const uint32_t i = tid < 4 ? tid : tail + (tid - 4);
         const bool ok = tid < 4 ? i < head : i < n;
         if (ok) {
-            const uint32_t key = key_to_ordered(keys[i], key_type);
+            const uint32_t key = TYPED ? key_to_ordered(keys[i], key_type) : keys[i];
 #pragma unroll
             for (uint32_t p = 0; p < PASSES; ++p)
                 atomicAdd(&s_h[p * RADIX + ((key >> (p * RADIX_BITS)) & (RADIX - 1))], 1u);
@@ -113,7 +115,7 @@ k_hist4(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hi
 // ---------------------------------------------------------------------------
 constexpr uint32_t HIST_COL_WORDS = PASSES * RADIX * 32;
 
-template <int THREADS>
+template <int THREADS, bool TYPED>
 __global__ void __launch_bounds__(THREADS, 1)
 k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
              uint4* __restrict__ clear, uint32_t clear_vec4, uint32_t key_type) {
@@ -134,7 +136,7 @@ k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
     const uint4* __restrict__ body = reinterpret_cast<const uint4*>(keys + head);
     uint32_t* const mycol = s_col + lane;
     auto count_key = [&](uint32_t key) {
-        key = key_to_ordered(key, key_type);
+        if (TYPED) key = key_to_ordered(key, key_type);
 #pragma unroll
         for (uint32_t p = 0; p < PASSES; ++p)
             atomicAdd(mycol + ((p * RADIX + ((key >> (p * RADIX_BITS)) & (RADIX - 1))) << 5), 1u);

@@ -60,29 +60,38 @@ static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, v
     if (knobs().hist_mode == HIST_COLUMNS) {
         constexpr int T = 1024;
         constexpr size_t SMEM = HIST_COL_WORDS * sizeof(uint32_t);
-        static uint64_t attr_on = 0;
+        auto kern = key_type != KEY_U32 ? k_hist4_cols<T, true> : k_hist4_cols<T, false>;
+        static uint64_t attr_on[2] = {0, 0};  // per instance, one bit per device
+        uint64_t& on = attr_on[key_type != KEY_U32 ? 1 : 0];
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
-        if (!((attr_on >> dev) & 1u)) {
-            if (cudaFuncSetAttribute(k_hist4_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (!((on >> dev) & 1u)) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM) != cudaSuccess)
                 return RS_ERR_CUDA;
-            attr_on |= 1ull << dev;
+            on |= 1ull << dev;
         }
         uint32_t grid = (uint32_t)di.sm_count;
         const uint32_t need = (vec4 + T - 1) / T;
         if (grid > need) grid = need > 0 ? need : 1;
         note_launch_begin(KK_HIST, stream);
-        k_hist4_cols<T><<<grid, T, SMEM, stream>>>(keys, n, hist, static_cast<uint4*>(clear),
-                                                    (uint32_t)(clear_bytes / sizeof(uint4)),
-                                                    key_type);
+        kern<<<grid, T, SMEM, stream>>>(keys, n, hist, static_cast<uint4*>(clear),
+                                         (uint32_t)(clear_bytes / sizeof(uint4)), key_type);
         note_launch_end(KK_HIST, stream);
         return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
     }
-    auto kern = k_hist4<HIST_THREADS, HIST_LEADER>;
+    const bool typed = key_type != KEY_U32;
+    auto kern = typed ? k_hist4<HIST_THREADS, HIST_LEADER, true>
+                      : k_hist4<HIST_THREADS, HIST_LEADER, false>;
     switch (knobs().hist_mode) {
-    case HIST_ATOMIC: kern = k_hist4<HIST_THREADS, HIST_ATOMIC>; break;
-    case HIST_MATCH: kern = k_hist4<HIST_THREADS, HIST_MATCH>; break;
+    case HIST_ATOMIC:
+        kern = typed ? k_hist4<HIST_THREADS, HIST_ATOMIC, true>
+                     : k_hist4<HIST_THREADS, HIST_ATOMIC, false>;
+        break;
+    case HIST_MATCH:
+        kern = typed ? k_hist4<HIST_THREADS, HIST_MATCH, true>
+                     : k_hist4<HIST_THREADS, HIST_MATCH, false>;
+        break;
     default: break;
     }
     note_launch_begin(KK_HIST, stream);
