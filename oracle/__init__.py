@@ -16,6 +16,8 @@ Every function follows the paper's definitions:
   counterpart; plain definition).
 * ``sort_pairs_threaded`` -- same result on several host threads, used to time
   the CPU baseline.
+* ``sort_pairs64`` -- the LSD radix sort of 64-bit keys (K = 64, D = 8: eight
+  passes), optionally carrying 32-bit values.
 * ``sort_typed`` / ``sort_typed_segmented`` -- stable sorts of signed 32-bit
   integer keys (by value) and of IEEE-754 binary32 keys (by the totalOrder
   predicate of IEEE 754-2008 Sec. 5.10): no paper counterpart; a plain merge
@@ -72,6 +74,9 @@ def _bind(path: str):
     lib.oracle_sort_pairs_threaded.argtypes = [_u32p, _u32p, _u32p, _u32p,
                                                ctypes.c_size_t, ctypes.c_uint]
     lib.oracle_sort_pairs_threaded.restype = ctypes.c_int
+    if hasattr(lib, "oracle_sort_pairs64"):
+        lib.oracle_sort_pairs64.argtypes = [_u64p, _u32p, _u64p, _u32p, ctypes.c_size_t]
+        lib.oracle_sort_pairs64.restype = ctypes.c_int
     if hasattr(lib, "oracle_sort_typed"):  # mutated copies of older sources lack it
         lib.oracle_sort_typed.argtypes = [_u32p, _u32p, _u32p, _u32p, ctypes.c_size_t,
                                           ctypes.c_int]
@@ -207,4 +212,20 @@ def sort_typed_segmented(keys, vals, offsets, key_type: str, lib=None):
         raise ValueError("malformed segment table")
     if rc:
         raise MemoryError("oracle_sort_typed_segmented failed (%d)" % rc)
+    return ko, vo
+
+
+def sort_pairs64(keys, vals, lib=None):
+    """Stable ascending LSD radix sort of uint64 keys (eight 8-bit passes),
+    values uint32 or None; returns new (keys, vals) arrays."""
+    keys = np.ascontiguousarray(keys)
+    if keys.dtype != np.uint64:
+        raise TypeError("expected uint64 keys, got %s" % keys.dtype)
+    vals = None if vals is None else _u32(vals)
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    rc = (lib or _load()).oracle_sort_pairs64(_ptr(keys, _u64p), _ptr(vals), _ptr(ko, _u64p),
+                                              _ptr(vo), keys.size)
+    if rc:
+        raise MemoryError("oracle_sort_pairs64 failed (%d)" % rc)
     return ko, vo

@@ -287,6 +287,46 @@ def pin_typed_segmented(lib=None):
             assert np.array_equal(ko[a:b], ek) and np.array_equal(vo[a:b], ev)
 
 
+# ---------------------------------------------------------------------------
+# 64-bit keys (K = 64, D = 8: eight passes, Sec. 4).
+# ---------------------------------------------------------------------------
+def _keys64(n, seed):
+    hi = inputs.splitmix32(seed, n, 0).astype(np.uint64)
+    lo = inputs.splitmix32(seed, n, 1).astype(np.uint64)
+    return (hi << np.uint64(32)) | lo
+
+
+def pin_sort64_numpy(lib=None):
+    """numpy's stable argsort of uint64 keys: random words, keys equal in the
+    low word only, keys equal in the high word only, and repeats."""
+    n = 6000
+    k = _keys64(n, 41)
+    k[::3] = (k[::3] & np.uint64(0xFFFFFFFF00000000)) | np.uint64(7)        # shared low word
+    k[1::5] = (k[1::5] & np.uint64(0xFFFFFFFF)) | np.uint64(0x5 << 40)       # shared high word
+    k[2::7] = k[0]
+    v = inputs.index_values(n)
+    ko, vo = oracle.sort_pairs64(k, v, lib=lib)
+    order = np.argsort(k, kind="stable")
+    assert np.array_equal(ko, k[order]) and np.array_equal(vo, v[order])
+
+
+def pin_sort64_bruteforce(lib=None):
+    """The closed-form stable rank on tiny arrays whose keys differ only in
+    the top byte, only in byte 4, or only in the bottom byte."""
+    for shift in (56, 32, 0):
+        for seed in range(3):
+            raw = inputs.splitmix32(50 + seed, 9, 0) % np.uint32(4)
+            k = raw.astype(np.uint64) << np.uint64(shift)
+            v = inputs.index_values(k.size)
+            ko, vo = oracle.sort_pairs64(k, v, lib=lib)
+            rank = stable_rank_bruteforce(k.tolist())
+            want_v = np.empty_like(v)
+            want_v[rank] = v
+            assert np.array_equal(vo, want_v) and np.array_equal(ko, k[vo])
+
+
+KEY64_PINS = (pin_sort64_numpy, pin_sort64_bruteforce)
+
 TYPED_PINS = (pin_typed_i32_numpy, pin_typed_f32_numpy, pin_typed_f32_total_order,
               pin_typed_stability, pin_typed_segmented)
 

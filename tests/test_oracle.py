@@ -120,3 +120,38 @@ def test_typed_pins_reject_mutant(name, tmp_path):
         except AssertionError:
             failures.append(pin.__name__)
     assert failures, "no pin rejects mutant %s" % name
+
+
+@pytest.mark.parametrize("pin", oracle_pins.KEY64_PINS, ids=lambda f: f.__name__)
+def test_key64_oracle_pin(pin):
+    pin()
+
+
+KEY64_MUTANTS = {
+    "only_four_passes": ("    for (unsigned p = 0; p < PASSES64; ++p) {\n        counting_pass64",
+                         "    for (unsigned p = 0; p < PASSES; ++p) {\n        counting_pass64"),
+    "digit_from_low_word": ("    return (uint32_t)((key >> (RADIX_BITS * p)) & (RADIX - 1u));",
+                            "    return (uint32_t)(((uint32_t)key >> (RADIX_BITS * (p & 3u))) & (RADIX - 1u));"),
+    "value_left_behind64": ("        if (vals_src != NULL) vals_dst[slot] = vals_src[i];",
+                            "        if (vals_src != NULL) vals_dst[i] = vals_src[i];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(KEY64_MUTANTS))
+def test_key64_pins_reject_mutant(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "rs_oracle.c")).read()
+    old, new = KEY64_MUTANTS[name]
+    assert src.count(old) == 1, "mutation anchor not found: %s" % name
+    mutated = tmp_path / ("%s.c" % name)
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / ("lib%s.so" % name)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                           "-o", str(so), str(mutated)])
+    lib = oracle._bind(str(so))
+    failures = []
+    for pin in oracle_pins.KEY64_PINS:
+        try:
+            pin(lib)
+        except AssertionError:
+            failures.append(pin.__name__)
+    assert failures, "no pin rejects mutant %s" % name
