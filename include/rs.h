@@ -134,6 +134,18 @@ rs_status rs_sort_segmented_typed_ex(uint32_t* d_keys, uint32_t* d_vals, size_t 
  * else the number of segments of a segmented call.  Pure host arithmetic. */
 size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments);
 
+/* 64-bit keys: the same LSD radix sort with K = 64 and D = 8 (Sec. 4 leaves
+ * the key width general), i.e. eight stable counting-sort passes, unsigned
+ * keys ascending, optionally carrying 32-bit values (d_vals may be NULL).
+ * Passes whose digit is the same for every key are skipped as for 32-bit
+ * keys (keys below 2^32 take four passes).  In place; asynchronous on
+ * cuda_stream; d_keys 8-byte aligned, d_vals 4-byte aligned, not overlapping;
+ * n < 2^32; workspace_bytes >= rs_workspace_bytes64(n, d_vals != NULL), the
+ * workspace 256-byte aligned.  Whole arrays only (no segmented form). */
+rs_status rs_sort64_ex(uint64_t* d_keys, uint32_t* d_vals, size_t n, void* cuda_stream,
+                       void* d_workspace, size_t workspace_bytes);
+size_t rs_workspace_bytes64(size_t n, int with_values);
+
 /* Synchronise cuda_stream (NULL = legacy default stream), then return and
  * clear the sticky device status word of the current device: RS_OK, or the
  * first device-side error recorded since the last call (RS_ERR_TIMEOUT,

@@ -17,6 +17,8 @@
    the same for every key makes its pass the identity, and it is skipped.
 3. Typed keys at 2^27 pairs of random 32-bit words (seed 21), read as
    signed integers and as IEEE floats (rs_sort_typed_ex).
+4. 64-bit keys with 32-bit values, 2^27 pairs of random words (seed 22),
+   eight passes (rs_sort64_ex).
 
 Prints one JSON line.
 """
@@ -155,6 +157,27 @@ def main(argv=None) -> int:
         typed[key_type] = {"ms": ms, "pairs_per_s": n / (ms / 1e3)}
         del k
     out["pairs_2^27_typed_keys"] = typed
+    del kb, vb, ws
+
+    # 4. 64-bit keys (eight passes) with 32-bit values, 2^27 pairs of random
+    # words (seed 22): 1 GiB of keys.
+    hi = inputs.splitmix32(22, n, 0).astype(np.uint64)
+    lo = inputs.splitmix32(22, n, 1).astype(np.uint64)
+    k = torch.from_numpy(((hi << np.uint64(32)) | lo).view(np.int64)).cuda()
+    del hi, lo
+    kb, vb = torch.empty_like(k), torch.empty_like(v)
+    nbytes = rs.workspace_bytes64(n, True)
+    raw = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    ws = raw[(-raw.data_ptr()) % 256:][:nbytes]
+
+    def restore():
+        kb.copy_(k)
+        vb.copy_(v)
+    ms = _timed(torch, stream, lambda: rs.sort64_ex(kb, vb, ws, stream), restore, a.steps,
+                a.warmup)
+    rs.check_stream()
+    out["pairs_2^27_key64_value32"] = {"ms": ms, "pairs_per_s": n / (ms / 1e3),
+                                       "bytes_per_pair_per_pass": 24, "passes": 8}
     print(json.dumps(out), flush=True)
     return 0
 

@@ -335,6 +335,28 @@ size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments) {
     return layout_for(n, with_values != 0).total;
 }
 
+size_t rs_workspace_bytes64(size_t n, int with_values) {
+    if (n == 0) return 0;
+    return layout_for64(n, with_values != 0).total;
+}
+
+rs_status rs_sort64_ex(uint64_t* d_keys, uint32_t* d_vals, size_t n, void* cuda_stream,
+                       void* d_workspace, size_t workspace_bytes) {
+    if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
+    if (n == 0) return RS_OK;
+    if (d_keys == nullptr || ((uintptr_t)d_keys & 7u) || ((uintptr_t)d_vals & 3u))
+        return RS_ERR_INVALID_ARG;
+    if (d_vals != nullptr) {
+        const uintptr_t k0 = (uintptr_t)d_keys, k1 = k0 + n * 8;
+        const uintptr_t v0 = (uintptr_t)d_vals, v1 = v0 + n * 4;
+        if (k0 < v1 && v0 < k1) return RS_ERR_INVALID_ARG;  // overlapping
+    }
+    if (d_workspace == nullptr || workspace_bytes < layout_for64(n, d_vals != nullptr).total)
+        return RS_ERR_INVALID_ARG;
+    return enqueue_sort64(reinterpret_cast<unsigned long long*>(d_keys), d_vals, (uint32_t)n,
+                          static_cast<cudaStream_t>(cuda_stream), d_workspace, workspace_bytes);
+}
+
 rs_status rs_stream_status(void* cuda_stream) {
     return sticky_status(static_cast<cudaStream_t>(cuda_stream));
 }

@@ -14,6 +14,7 @@ namespace rs {
 constexpr uint32_t RADIX_BITS = 8;                 // D = 8 (Sec. 4, Alg. 2)
 constexpr uint32_t RADIX = 1u << RADIX_BITS;       // 256 buckets per pass
 constexpr uint32_t PASSES = 4;                     // K / D with K = 32
+constexpr uint32_t PASSES64 = 8;                   // K / D with K = 64 (64-bit keys)
 
 // Error bits recorded on the device: in ctrl->err for the running call and
 // in the per-device sticky word that rs_stream_status reads and clears (its
@@ -33,11 +34,12 @@ constexpr uint32_t DIR_B_TO_A = 2; // alternate buffers -> caller's arrays
 
 // Per-call control block, zeroed by one cudaMemsetAsync at the start of a
 // call.  Lives at the start of the workspace.
-// Plan slots: the LSD passes 0..3, and MSD_SLOT for the most-significant-digit
-// pass of the MSD-first order (Alg. 2), which runs before the passes 0..3 are
-// reached and, when the plan chooses it, makes them all DIR_SKIP.
-constexpr uint32_t MSD_SLOT = PASSES;
-constexpr uint32_t PLAN_SLOTS = PASSES + 1;
+// Plan slots: the LSD passes 0..7 (0..3 for 32-bit keys), and MSD_SLOT for
+// the most-significant-digit pass of the MSD-first order (Alg. 2), which runs
+// before the passes 0..3 are reached and, when the plan chooses it, makes them
+// all DIR_SKIP.
+constexpr uint32_t MSD_SLOT = PASSES64;
+constexpr uint32_t PLAN_SLOTS = PASSES64 + 1;
 
 struct Ctrl {
     uint32_t err;                  // error bits of this call
@@ -47,9 +49,9 @@ struct Ctrl {
     uint32_t small_count;          // segmented sorts (and MSD buckets): one-CTA segments
     uint32_t large_count;          // segmented sorts: number of large segments
     uint32_t tiny_count;           // segmented sorts (and MSD buckets): one-warp segments
-    uint32_t pad[1];               // keep hist 64-byte aligned
-    uint32_t hist[PASSES][RADIX];  // digit histograms (H)
-    uint32_t gofs[PASSES][RADIX];  // first output slot of every bucket (G)
+    uint32_t pad[9];               // keep hist 64-byte aligned
+    uint32_t hist[PASSES64][RADIX];  // digit histograms (H); 0..3 for 32-bit keys
+    uint32_t gofs[PASSES64][RADIX];  // first output slot of every bucket (G)
 };
 static_assert(offsetof(Ctrl, hist) % 64 == 0, "histograms 64-byte aligned");
 
@@ -118,6 +120,16 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
 __device__ __forceinline__ void cp_async4(uint32_t* smem_dst, const uint32_t* gmem_src) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(unsigned long long* smem_dst,
+                                          const unsigned long long* gmem_src) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+// The same copy for either key width.
+__device__ __forceinline__ void cp_async_elem(uint32_t* d, const uint32_t* s) { cp_async4(d, s); }
+__device__ __forceinline__ void cp_async_elem(unsigned long long* d, const unsigned long long* s) {
+    cp_async8(d, s);
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");

@@ -183,39 +183,50 @@ k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
 // are listed in tiny_list (one-warp sort), larger ones in small_list
 // (one-CTA sort).
 // ---------------------------------------------------------------------------
+template <int NPASS>
 __global__ void __launch_bounds__(1024)
 k_plan(Ctrl* __restrict__ ctrl, uint32_t n, uint32_t msd_allowed, uint32_t warp_max,
        uint32_t bucket_cap, uint32_t* __restrict__ msd_off, uint32_t* __restrict__ tiny_list,
        uint32_t* __restrict__ small_list) {
+    static_assert(NPASS == 4 || NPASS == 8, "32-bit or 64-bit keys");
     __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_trivial[PASSES];
+    __shared__ uint32_t s_trivial[NPASS];
     __shared__ uint32_t s_big;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t p = tid >> 8, b = tid & (RADIX - 1);
-    if (tid < PASSES) s_trivial[tid] = 0;
+    const uint32_t b = tid & (RADIX - 1);
+    if (tid < NPASS) s_trivial[tid] = 0;
     if (tid == 0) s_big = 0;
-    const uint32_t h = ctrl->hist[p][b];
-    uint32_t x = h;
+    // Thread (p, b): p = tid / 256 (+ 4 in the second round for 64-bit keys).
+    uint32_t h3 = 0, first3 = 0;  // digit 3, for the MSD-first order
+    for (uint32_t round = 0; round < NPASS / 4; ++round) {
+        const uint32_t p = (tid >> 8) + 4 * round;
+        const uint32_t h = ctrl->hist[p][b];
+        uint32_t x = h;
 #pragma unroll
-    for (uint32_t o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t off = 0;
+        for (uint32_t w = (tid >> 8) * (RADIX / 32); w < warp; ++w) off += s_warp[w];
+        const uint32_t first = off + x - h;
+        ctrl->gofs[p][b] = first;
+        if (h == n) s_trivial[p] = 1;
+        if (p == PASSES - 1) {
+            h3 = h;
+            first3 = first;
+            if (h > bucket_cap) s_big = 1;
+        }
+        __syncthreads();  // s_warp is reused by the next round
     }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    uint32_t off = 0;
-    for (uint32_t w = p * (RADIX / 32); w < warp; ++w) off += s_warp[w];
-    const uint32_t first = off + x - h;
-    ctrl->gofs[p][b] = first;
-    if (h == n) s_trivial[p] = 1;
-    if (p == PASSES - 1 && h > bucket_cap) s_big = 1;
-    __syncthreads();
-    const bool msd = msd_allowed && !s_trivial[PASSES - 1] && !s_big;
-    if (msd && p == PASSES - 1) {
-        msd_off[b] = first;
+    const bool msd = NPASS == 4 && msd_allowed && !s_trivial[PASSES - 1] && !s_big;
+    if (msd && (tid >> 8) == PASSES - 1) {
+        msd_off[b] = first3;
         if (b == RADIX - 1) msd_off[RADIX] = n;
-        if (h > 0) {
-            if (h <= warp_max)
+        if (h3 > 0) {
+            if (h3 <= warp_max)
                 tiny_list[atomicAdd(&ctrl->tiny_count, 1u)] = b;
             else
                 small_list[atomicAdd(&ctrl->small_count, 1u)] = b;
@@ -226,17 +237,17 @@ k_plan(Ctrl* __restrict__ ctrl, uint32_t n, uint32_t msd_allowed, uint32_t warp_
         ctrl->dir[MSD_SLOT] = DIR_A_TO_B;
     } else if (tid == 0) {
         ctrl->dir[MSD_SLOT] = DIR_SKIP;
-        uint32_t trivial[PASSES], executed = 0;
-        for (uint32_t q = 0; q < PASSES; ++q) {
+        uint32_t trivial[NPASS], executed = 0;
+        for (uint32_t q = 0; q < NPASS; ++q) {
             trivial[q] = s_trivial[q];
             executed += trivial[q] ? 0 : 1;
         }
         if (executed & 1) {
-            for (uint32_t q = 0; q < PASSES; ++q)
+            for (uint32_t q = 0; q < NPASS; ++q)
                 if (trivial[q]) { trivial[q] = 0; break; }
         }
         uint32_t parity = 0;
-        for (uint32_t q = 0; q < PASSES; ++q) {
+        for (uint32_t q = 0; q < NPASS; ++q) {
             if (trivial[q]) {
                 ctrl->dir[q] = DIR_SKIP;
             } else {
@@ -244,6 +255,38 @@ k_plan(Ctrl* __restrict__ ctrl, uint32_t n, uint32_t msd_allowed, uint32_t warp_
                 parity ^= 1;
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_hist8: the eight digit histograms of 64-bit keys (K = 64, D = 8) in one
+// read of the keys, added into hist[p * 256 + b] (zeroed by the caller), via
+// a CTA-private shared histogram.  Also clears the first pass's status array.
+// ---------------------------------------------------------------------------
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_hist8(const unsigned long long* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
+        uint4* __restrict__ clear, uint32_t clear_vec4) {
+    __shared__ uint32_t s_h[PASSES64 * RADIX];
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t i = tid; i < PASSES64 * RADIX; i += THREADS) s_h[i] = 0;
+    const uint32_t gtid = blockIdx.x * THREADS + tid;
+    const uint32_t gsize = gridDim.x * THREADS;
+    for (uint32_t i = gtid; i < clear_vec4; i += gsize) clear[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    for (uint32_t i = gtid; i < n; i += gsize) {
+        const unsigned long long k = __ldcs(keys + i);
+        const uint32_t lo = (uint32_t)k, hi = (uint32_t)(k >> 32);
+#pragma unroll
+        for (uint32_t p = 0; p < 4; ++p) {
+            atomicAdd(&s_h[p * RADIX + ((lo >> (8 * p)) & (RADIX - 1))], 1u);
+            atomicAdd(&s_h[(p + 4) * RADIX + ((hi >> (8 * p)) & (RADIX - 1))], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < PASSES64 * RADIX; i += THREADS) {
+        const uint32_t c = s_h[i];
+        if (c) atomicAdd(hist + i, c);
     }
 }
 

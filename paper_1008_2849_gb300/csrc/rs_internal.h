@@ -113,6 +113,11 @@ Layout layout_for(size_t n, bool pairs);
 rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
                        void* workspace, size_t workspace_bytes, uint32_t key_type = 0);
 
+// 64-bit keys (eight passes), optionally carrying 32-bit values.
+Layout layout_for64(size_t n, bool pairs);
+rs_status enqueue_sort64(unsigned long long* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
+                         void* workspace, size_t workspace_bytes);
+
 // Enqueue the digit histograms of n keys into hist[4 * 256] (zeroed first).
 rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
                              cudaStream_t stream);

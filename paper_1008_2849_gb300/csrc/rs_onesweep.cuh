@@ -13,7 +13,8 @@
 namespace rs {
 
 // ---------------------------------------------------------------------------
-// Shared-memory plan of k_onesweep (all in 32-bit words):
+// Shared-memory plan of k_onesweep (offsets in 32-bit words; KW = words per
+// key, 1 for 32-bit keys and 2 for 64-bit keys):
 //   in_k[2][TILE]        input keys of the current and the next tile; the
 //                        current tile's values are staged here once its keys
 //                        are ranked
@@ -23,14 +24,16 @@ namespace rs {
 //                        tile positions while the tile is ranked
 //   mask[WARPS][RADIX]   per-warp peer masks of the ranking (zero between uses)
 // ---------------------------------------------------------------------------
-template <int THREADS, int ITEMS, bool PAIRS>
+template <int THREADS, int ITEMS, bool PAIRS, int KW = 1>
 struct OnesweepSmem {
     static constexpr uint32_t WARPS = THREADS / 32;
     static constexpr uint32_t TILE = THREADS * ITEMS;
     static constexpr uint32_t IN_K = 0;
-    static constexpr uint32_t IN_V = IN_K + 2 * TILE;
+    static constexpr uint32_t IN_V = IN_K + 2 * TILE * KW;
     static constexpr uint32_t STG = IN_V + (PAIRS ? TILE : 0);
-    static constexpr uint32_t WCNT = STG + TILE;
+    static constexpr uint32_t WCNT = STG + TILE * KW;
+    static_assert(KW == 1 || ((TILE * KW) % 4 == 0 && STG % KW == 0),
+                  "key buffers 16-byte aligned for the bulk copies, stage aligned to keys");
     static constexpr uint32_t MASK = WCNT + WARPS * RADIX;
     static constexpr uint32_t WORDS = MASK + WARPS * RADIX;
     static constexpr size_t BYTES = WORDS * sizeof(uint32_t);
@@ -94,17 +97,18 @@ struct OnesweepSmem {
 // of the large segments; seg_gofs[s][pass][b] is the absolute first output
 // slot of bucket b of segment s; the number of tiles is ctrl->seg_tiles.
 template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WINDOW, bool SEG,
-          bool TYPED>
+          bool TYPED, typename K = uint32_t>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
-k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
-           uint32_t* __restrict__ kb, uint32_t* __restrict__ vb,
+k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
+           K* __restrict__ kb, uint32_t* __restrict__ vb,
            uint32_t n, uint32_t pass, uint32_t slot, uint32_t num_tiles, Ctrl* __restrict__ ctrl,
            uint32_t* __restrict__ sticky, S* __restrict__ status, S* __restrict__ status_clear,
            uint32_t clear_words, uint32_t spin_limit, uint32_t debug,
            const uint4* __restrict__ tile_geo, const uint32_t* __restrict__ seg_gofs,
            uint32_t key_type) {
-    using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
+    using L = OnesweepSmem<THREADS, ITEMS, PAIRS, (int)(sizeof(K) / 4)>;
     using SW = StatusWord<S>;
+    static_assert(sizeof(K) == 4 || !TYPED, "typed keys are 32-bit");
     static_assert(THREADS >= (int)RADIX && THREADS % 32 == 0, "one thread per digit");
     static_assert(RADIX_BITS == 8, "digits are whole bytes of the key");
     constexpr uint32_t WARPS = L::WARPS;
@@ -125,7 +129,8 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
 
     extern __shared__ uint4 s_dyn[];
     uint32_t* const smem = reinterpret_cast<uint32_t*>(s_dyn);
-    uint32_t* const s_stage = smem + L::STG;
+    K* const s_stage = reinterpret_cast<K*>(smem + L::STG);
+    K* const s_keys = reinterpret_cast<K*>(smem + L::IN_K);  // [2][TILE]
     uint32_t* const s_wcnt = smem + L::WCNT;
     const uint32_t* const s_in_v = smem + L::IN_V;
     __shared__ uint32_t s_gbase[RADIX];  // G[pass][b]
@@ -166,9 +171,12 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         map_in = first ? key_type : KEY_U32;
         map_out = last ? key_type : KEY_U32;
     }
-    auto read_key = [map_in](uint32_t k) { return TYPED ? key_to_ordered(k, map_in) : k; };
-    const uint32_t* __restrict__ src_k = dir == DIR_A_TO_B ? ka : kb;
-    uint32_t* __restrict__ dst_k = dir == DIR_A_TO_B ? kb : ka;
+    auto read_key = [map_in](K k) -> K {
+        if constexpr (TYPED) return key_to_ordered(k, map_in);
+        else return k;
+    };
+    const K* __restrict__ src_k = dir == DIR_A_TO_B ? ka : kb;
+    K* __restrict__ dst_k = dir == DIR_A_TO_B ? kb : ka;
     const uint32_t* __restrict__ src_v = dir == DIR_A_TO_B ? va : vb;
     uint32_t* __restrict__ dst_v = dir == DIR_A_TO_B ? vb : va;
 
@@ -194,20 +202,23 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
 
     // Start copying the g.y items from src + g.x into dst (collective): the
     // 16-byte-aligned middle by one bulk copy, the few items before and after
-    // it by per-thread copies, all completing on `bar`.
-    auto issue_copy = [&](uint32_t* dst, const uint32_t* src, uint4 g, uint64_t* bar) {
+    // it by per-thread copies, all completing on `bar`.  Items are keys (K)
+    // or values (32-bit).
+    auto issue_copy = [&](auto* dst, const auto* src, uint4 g, uint64_t* bar) {
+        using T = std::remove_cv_t<std::remove_pointer_t<decltype(src)>>;
+        constexpr uint32_t PER16 = 16 / sizeof(T);  // items per 16 bytes
         const uint32_t valid = g.y;
-        const uint32_t* from = src + g.x;
+        const T* from = src + g.x;
         // Items before the first 16-byte boundary of the source; the bulk copy
         // needs the same alignment on both sides, so it is used only when the
         // destination offset agrees.
-        const uint32_t head = (uint32_t)((16u - ((uintptr_t)from & 15u)) & 15u) >> 2;
-        const bool bulk_ok = head == 0 && valid >= 4;
-        const uint32_t nb = bulk_ok ? (valid & ~3u) : 0u;
+        const uint32_t head = (uint32_t)((16u - ((uintptr_t)from & 15u)) & 15u) / sizeof(T);
+        const bool bulk_ok = head == 0 && valid >= PER16;
+        const uint32_t nb = bulk_ok ? (valid & ~(PER16 - 1)) : 0u;
         if (nb < valid) {  // CTA-uniform
             bool issued = false;
             for (uint32_t i = nb + tid; i < valid; i += THREADS) {
-                cp_async4(dst + i, from + i);
+                cp_async_elem(dst + i, from + i);
                 issued = true;
             }
             if (issued) cp_async_mbar_arrive(bar);
@@ -217,8 +228,8 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             // The buffer was last written by ordinary stores: order those
             // before the bulk copy's writes.
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, nb * 4u);
-            if (nb) tma_load_1d(dst, from, nb * 4u, bar);
+            mbar_arrive_expect_tx(bar, nb * (uint32_t)sizeof(T));
+            if (nb) tma_load_1d(dst, from, nb * (uint32_t)sizeof(T), bar);
         }
     };
 
@@ -235,13 +246,23 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         phase ^= 1u << b;
     };
     // Digit of a key: byte `pass`, picked by one byte permute (the other
-    // three result bytes come from the zero operand).
-    const uint32_t dsel = 0x4440u | pass;
-    auto digit_of = [dsel](uint32_t key) { return __byte_perm(key, 0u, dsel); };
+    // three result bytes come from the zero operand) from the key's word
+    // that holds it.
+    const uint32_t dsel = 0x4440u | (pass & 3u);
+    const bool high_word = pass >= 4;
+    auto digit_of = [dsel, high_word](K key) {
+        if constexpr (sizeof(K) == 4) {
+            (void)high_word;
+            return __byte_perm(key, 0u, dsel);
+        } else {
+            const uint32_t w = high_word ? (uint32_t)(key >> 32) : (uint32_t)key;
+            return __byte_perm(w, 0u, dsel);
+        }
+    };
     const uint32_t wofs = warp * WARP_ITEMS;
     // Count the slots of warp w of the tile in key buffer b into wcnt row w.
     auto count_slots_of = [&](uint32_t b, uint32_t valid, uint32_t w) {
-        const uint32_t* keys = smem + L::IN_K + b * TILE + w * WARP_ITEMS + lane;
+        const K* keys = s_keys + b * TILE + w * WARP_ITEMS + lane;
         uint32_t* row = s_wcnt + w * RADIX;
         if (valid == TILE) {
 #pragma unroll
@@ -299,7 +320,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
     // Prologue: the first tile's data and counts; the second tile's id is taken
     // once they are published.
     if (s_ids[0] >= num_tiles) return;
-    issue_copy(smem + L::IN_K, src_k, s_geo[0], &s_bar[0]);
+    issue_copy(s_keys, src_k, s_geo[0], &s_bar[0]);
     if (PAIRS) issue_copy(smem + L::IN_V, src_v, s_geo[0], &s_bar[2]);
     wait_bar(0);
     count_slots_of(0, s_geo[0].y, warp);
@@ -321,7 +342,7 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         const uint4 geo = s_geo[it & 3];
         const uint4 ngeo = s_geo[(it + 1) & 3];
         const bool have_next = nxt < num_tiles;
-        if (have_next) issue_copy(smem + L::IN_K + (buf ^ 1) * TILE, src_k, ngeo, &s_bar[buf ^ 1]);
+        if (have_next) issue_copy(s_keys + (buf ^ 1) * TILE, src_k, ngeo, &s_bar[buf ^ 1]);
         // Segmented: this tile's bucket bases, fetched now, used after ranking.
         uint32_t seg_base = 0;
         if (SEG && tid < RADIX) seg_base = seg_gofs[((size_t)geo.w * PASSES + pass) * RADIX + tid];
@@ -332,7 +353,8 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
 
         const uint32_t valid = geo.y;
         const uint32_t first_tile = geo.z;  // look-back stops here
-        uint32_t* const in_k = smem + L::IN_K + buf * TILE;
+        K* const in_k = s_keys + buf * TILE;
+        uint32_t* const in_kv = reinterpret_cast<uint32_t*>(in_k);  // staged values
 
         // ---- 2. rank, and stage the keys ------------------------------------
         uint32_t* const cnt = s_wcnt + warp * RADIX;
@@ -341,12 +363,12 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
         auto rank_tile = [&](auto full) {
             constexpr bool FULL = decltype(full)::value;
             const uint32_t left = FULL ? WARP_ITEMS : (valid > wofs ? valid - wofs : 0u);
-            const uint32_t* keys = in_k + wofs + lane;
+            const K* keys = in_k + wofs + lane;
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
                 const bool is_live = FULL || j * 32 + lane < left;
                 const uint32_t live = FULL ? 0xffffffffu : prefix_lanes(j * 32, left);
-                const uint32_t k = read_key(keys[j * 32]);
+                const K k = read_key(keys[j * 32]);
                 const uint32_t d = digit_of(k);
                 uint32_t peers;
                 if (j & 1) {
@@ -471,11 +493,11 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             for (int j = 0; j < ITEMS; ++j) vv[j] = s_in_v[wofs + j * 32 + lane];
             if (valid == TILE) {
 #pragma unroll
-                for (int j = 0; j < ITEMS; ++j) in_k[pos[j]] = vv[j];
+                for (int j = 0; j < ITEMS; ++j) in_kv[pos[j]] = vv[j];
             } else {
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j)
-                    if (wofs + j * 32 + lane < valid) in_k[pos[j]] = vv[j];
+                    if (wofs + j * 32 + lane < valid) in_kv[pos[j]] = vv[j];
             }
         }
         __syncthreads();
@@ -492,11 +514,12 @@ k_onesweep(uint32_t* __restrict__ ka, uint32_t* __restrict__ va,
             constexpr bool FULL = decltype(full)::value;
             auto store_slot = [&](uint32_t s) {
                 if (FULL || s < valid) {
-                    const uint32_t kk = s_stage[s];
+                    const K kk = s_stage[s];
                     const uint32_t g = s_gofs[digit_of(kk)] + s;
                     if (g < n) {
-                        dst_k[g] = TYPED ? key_from_ordered(kk, map_out) : kk;
-                        if (PAIRS) dst_v[g] = in_k[s];
+                        if constexpr (TYPED) dst_k[g] = key_from_ordered(kk, map_out);
+                        else dst_k[g] = kk;
+                        if (PAIRS) dst_v[g] = in_kv[s];
                     } else {
                         bad = true;
                     }

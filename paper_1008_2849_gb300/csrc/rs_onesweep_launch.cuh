@@ -17,15 +17,15 @@ RS_TILE_SHAPES(RS_SHAPE_STRUCT)
 #undef RS_SHAPE_STRUCT
 
 template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S, bool SEG,
-          bool TYPED>
-static rs_status launch_onesweep_shape(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
+          bool TYPED, typename K = uint32_t>
+static rs_status launch_onesweep_shape(K* ka, uint32_t* va, K* kb, uint32_t* vb,
                                        uint32_t n, uint32_t pass, uint32_t slot, Ctrl* ctrl,
                                        uint32_t* sticky,
                                        void* status, void* status_clear, const SegView& seg,
                                        uint32_t key_type, cudaStream_t stream) {
-    using L = OnesweepSmem<THREADS, ITEMS, PAIRS>;
+    using L = OnesweepSmem<THREADS, ITEMS, PAIRS, (int)(sizeof(K) / 4)>;
     constexpr uint32_t TILE = L::TILE;
-    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW, SEG, TYPED>;
+    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW, SEG, TYPED, K>;
     static int ctas_per_sm[64] = {0};  // per device: resident CTAs per SM
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;

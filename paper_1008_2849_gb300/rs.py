@@ -45,6 +45,8 @@ SIGNATURES = {
     "rs_sort_typed_ex": (_int, [_vp, _vp, _sz, _int, _vp, _vp, _sz]),
     "rs_sort_segmented_typed_ex": (_int, [_vp, _vp, _sz, _vp, _u32, _int, _vp, _vp, _sz]),
     "rs_workspace_bytes": (_sz, [_sz, _int, _u32]),
+    "rs_sort64_ex": (_int, [_vp, _vp, _sz, _vp, _vp, _sz]),
+    "rs_workspace_bytes64": (_sz, [_sz, _int]),
     "rs_stream_status": (_int, [_vp]),
     "rs_status_string": (ctypes.c_char_p, [_int]),
     "rs_digit_histograms_ex": (_int, [_vp, _sz, _vp, _vp]),
@@ -101,14 +103,14 @@ def _check(code: int, where: str):
         raise RsError(code, where)
 
 
-def _dev_ptr(t, name: str) -> int:
+def _dev_ptr(t, name: str, width: int = 4) -> int:
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a torch.Tensor" % name)
     if not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
-    if t.element_size() != 4 or t.dtype.is_floating_point:
-        raise TypeError("%s must hold 4-byte integers (int32/uint32), got %s" % (name, t.dtype))
+    if t.element_size() != width or t.dtype.is_floating_point:
+        raise TypeError("%s must hold %d-byte integers, got %s" % (name, width, t.dtype))
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
     return t.data_ptr()
@@ -200,6 +202,31 @@ def sort_pairs_segmented_ex(keys, vals, offsets, workspace, stream=None) -> None
                                             keys.numel(), op, ns, _stream_handle(stream),
                                             workspace.data_ptr(), workspace.numel()),
            "rs_sort_pairs_segmented_ex")
+
+
+def workspace_bytes64(n: int, with_values: bool) -> int:
+    return int(lib().rs_workspace_bytes64(n, 1 if with_values else 0))
+
+
+def sort64_ex(keys, vals, workspace, stream=None) -> None:
+    """Enqueue an in-place sort of 64-bit keys (an int64 CUDA tensor holding
+    the uint64 bit patterns), with int32 values or None."""
+    if vals is not None and vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    _check(lib().rs_sort64_ex(_dev_ptr(keys, "keys", 8),
+                              None if vals is None else _dev_ptr(vals, "vals"), keys.numel(),
+                              _stream_handle(stream), workspace.data_ptr(), workspace.numel()),
+           "rs_sort64_ex")
+
+
+def sort64(keys, vals=None, stream=None) -> None:
+    """Synchronous 64-bit key sort with a workspace allocated for the call."""
+    import torch
+    nbytes = max(workspace_bytes64(keys.numel(), vals is not None), 1)
+    raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=keys.device)
+    pad = (-raw.data_ptr()) % 256
+    sort64_ex(keys, vals, raw[pad:pad + nbytes], stream)
+    check_stream(stream)
 
 
 KEY_TYPES = {"u32": 0, "i32": 1, "f32": 2}

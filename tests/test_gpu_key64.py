@@ -1,0 +1,114 @@
+"""GPU parity tests of the 64-bit key sort (K = 64, D = 8: eight passes)
+against the CPU oracle's 64-bit LSD sort, element by element."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1008_2849_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1008_2849_gb300 import build, rs as _rs
+    build.build_library()
+    _rs.lib()
+    return _rs
+
+
+def _keys64(kind, n, seed):
+    hi = inputs.splitmix32(seed, n, 0).astype(np.uint64)
+    lo = inputs.splitmix32(seed, n, 1).astype(np.uint64)
+    if kind == "uniform":
+        return (hi << np.uint64(32)) | lo
+    if kind == "low_word":        # keys below 2^32: passes 4..7 are skipped
+        return lo
+    if kind == "high_word":       # low word constant: passes 0..3 are skipped
+        return (hi << np.uint64(32)) | np.uint64(0x1234)
+    if kind == "and2":            # bit-one probability 1/4 in every byte
+        h2 = inputs.splitmix32(seed, n, 2).astype(np.uint64)
+        l2 = inputs.splitmix32(seed, n, 3).astype(np.uint64)
+        return ((hi & h2) << np.uint64(32)) | (lo & l2)
+    if kind == "equal":
+        return np.full(n, 0xDEADBEEF01234567, dtype=np.uint64)
+    raise ValueError(kind)
+
+
+def _dev(a):
+    import torch
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).cuda()
+    return torch.from_numpy(a.view(np.int32)).cuda()
+
+
+def _host(t, dtype):
+    return t.cpu().numpy().view(dtype)
+
+
+def _check(rs, k, with_values=True):
+    v = inputs.index_values(k.size) if with_values else None
+    kd = _dev(k)
+    vd = _dev(v) if with_values else None
+    rs.sort64(kd, vd)
+    ko, vo = oracle.sort_pairs64(k, v)
+    assert np.array_equal(_host(kd, np.uint64), ko)
+    if with_values:
+        assert np.array_equal(_host(vd, np.uint32), vo)
+
+
+@pytest.mark.parametrize("n", [1, 2, 100, 2687, 2688, 2689, 8193, 70_001, (1 << 20) + 37])
+def test_key64_sizes(rs, n):
+    """One partial tile, exactly one tile (384 x 7), several tiles, a ragged
+    tail; pairs and keys only."""
+    k = _keys64("uniform", n, seed=170 + n % 83)
+    _check(rs, k)
+    _check(rs, k, with_values=False)
+
+
+@pytest.mark.parametrize("kind", ["low_word", "high_word", "and2", "equal"])
+def test_key64_distributions(rs, kind):
+    """Keys whose low or high words are constant (four passes skipped), skewed
+    bytes, and all keys equal (no pass moves data)."""
+    _check(rs, _keys64(kind, (1 << 20) + 5, seed=180))
+
+
+def test_key64_2pow24_full(rs):
+    k = _keys64("uniform", 1 << 24, seed=190)
+    _check(rs, k)
+
+
+def test_key64_2pow27_properties(rs):
+    """2^27 pairs (1 GiB of keys): nondecreasing, a permutation carried by
+    the values (value = input index), and stable."""
+    n = 1 << 27
+    k = _keys64("and2", n, seed=191)
+    v = inputs.index_values(n)
+    kd, vd = _dev(k), _dev(v)
+    rs.sort64(kd, vd)
+    ko, vo = _host(kd, np.uint64), _host(vd, np.uint32)
+    assert np.all(ko[1:] >= ko[:-1])
+    assert np.array_equal(k[vo], ko)
+    same = ko[1:] == ko[:-1]
+    assert np.all(vo[1:][same] > vo[:-1][same])
+    assert np.array_equal(np.sort(vo), v)
+
+
+def test_key64_argument_errors(rs):
+    import ctypes
+    import torch
+    k = torch.zeros(16, dtype=torch.int64, device="cuda")
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    L = rs.lib()
+    # misaligned keys
+    code = L.rs_sort64_ex(ctypes.c_void_p(k.data_ptr() + 4), None, 8, None,
+                          ctypes.c_void_p(ws.data_ptr()), ws.numel())
+    assert code == 1
+    # workspace too small
+    code = L.rs_sort64_ex(ctypes.c_void_p(k.data_ptr()), None, 16, None,
+                          ctypes.c_void_p(ws.data_ptr()), 16)
+    assert code == 1

@@ -226,10 +226,11 @@ def test_wide_status_2pow30_plus(rs):
 
 def _plan_slots_used(ws):
     """Tiles taken per plan slot by the last sort that used workspace `ws`:
-    the control block sits at the start of the workspace (err, then the
-    five tile counters: LSD passes 0..3 and the MSD pass)."""
-    head = ws[:24].cpu().numpy().view(np.uint32)
-    return head[1:6].tolist()
+    the control block sits at the start of the workspace (err, then nine
+    tile counters: LSD passes 0..7 -- 0..3 for 32-bit keys -- and the MSD
+    pass).  Returns [passes 0..3, MSD pass]."""
+    head = ws[:40].cpu().numpy().view(np.uint32)
+    return head[1:5].tolist() + [int(head[9])]
 
 
 def _msd_keys(kind, n, seed):
