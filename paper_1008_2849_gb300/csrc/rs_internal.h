@@ -3,6 +3,7 @@
 // of the ABI.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -177,5 +178,27 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
                                  uint32_t key_type = 0);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// One bit per device (ordinal < 64) for one-time host setup of a kernel
+// (its shared-memory limit), safe when several host threads enqueue sorts.
+struct DeviceOnce {
+    std::atomic<uint64_t> bits{0};
+    bool done(int dev) const { return (bits.load(std::memory_order_acquire) >> dev) & 1u; }
+    void mark(int dev) { bits.fetch_or(uint64_t(1) << dev, std::memory_order_release); }
+};
+
+// Raise the dynamic shared-memory limit of `kern` to `bytes` once per device.
+template <typename Kern>
+rs_status allow_smem_once(Kern kern, size_t bytes, DeviceOnce& once) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RS_ERR_CUDA;
+    if (!once.done(dev)) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess)
+            return RS_ERR_CUDA;
+        once.mark(dev);
+    }
+    return RS_OK;
+}
 
 }  // namespace rs

@@ -26,26 +26,26 @@ static rs_status launch_onesweep_shape(K* ka, uint32_t* va, K* kb, uint32_t* vb,
     using L = OnesweepSmem<THREADS, ITEMS, PAIRS, (int)(sizeof(K) / 4)>;
     constexpr uint32_t TILE = L::TILE;
     auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW, SEG, TYPED, K>;
-    static int ctas_per_sm[64] = {0};  // per device: resident CTAs per SM
+    static std::atomic<int> ctas_per_sm[64];  // per device: resident CTAs per SM (0: unknown)
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
-    if (ctas_per_sm[dev] == 0) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RS_ERR_CUDA;
+    int resident = ctas_per_sm[dev].load(std::memory_order_acquire);
+    if (resident == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES) !=
             cudaSuccess)
             return RS_ERR_CUDA;
-        int blocks = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, THREADS, L::BYTES) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, THREADS, L::BYTES) !=
                 cudaSuccess ||
-            blocks < 1)
+            resident < 1)
             return RS_ERR_CUDA;
-        ctas_per_sm[dev] = blocks;
+        ctas_per_sm[dev].store(resident, std::memory_order_release);
     }
     DeviceInfo di;
     rs_status st = device_info(&di);
     if (st != RS_OK) return st;
     // Segmented: the tile count is only known on the device (ctrl->seg_tiles).
     const uint32_t tiles = SEG ? seg.max_tiles : (uint32_t)((n + (size_t)TILE - 1) / TILE);
-    uint32_t grid = (uint32_t)(di.sm_count * ctas_per_sm[dev]);
+    uint32_t grid = (uint32_t)(di.sm_count * resident);
     if (grid > tiles) grid = tiles;
     if (grid == 0) return RS_OK;
     note_launch_begin(SEG ? KK_SEG_ONESWEEP : KK_ONESWEEP, stream);

@@ -7,20 +7,6 @@ namespace rs {
 
 namespace {
 
-// Raise the dynamic shared-memory limit of `kern` once per device.
-template <typename K>
-rs_status allow_smem(K kern, size_t bytes, uint64_t* attr_on) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
-    if (!((*attr_on >> dev) & 1u)) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-            cudaSuccess)
-            return RS_ERR_CUDA;
-        *attr_on |= 1ull << dev;
-    }
-    return RS_OK;
-}
-
 // One-CTA sort shapes: 256 threads x 16 items (4096) and 512 x 16 (8192).
 template <int THREADS, int ITEMS, int BITS, bool PAIRS>
 rs_status launch_small_shape(uint32_t* keys, uint32_t* vals, const uint32_t* src_keys,
@@ -31,8 +17,8 @@ rs_status launch_small_shape(uint32_t* keys, uint32_t* vals, const uint32_t* src
     constexpr size_t SMEM =
         ((PAIRS ? 4u : 2u) * CAP + (THREADS / 32) * (1u << BITS)) * sizeof(uint32_t);
     auto kern = k_small_sort<THREADS, ITEMS, BITS, PAIRS>;
-    static uint64_t attr_on = 0;  // one bit per device with the attribute set
-    rs_status st = allow_smem(kern, SMEM, &attr_on);
+    static DeviceOnce smem_set;
+    rs_status st = allow_smem_once(kern, SMEM, smem_set);
     if (st != RS_OK) return st;
     note_launch_begin(KK_SMALL, stream);
     kern<<<grid, THREADS, SMEM, stream>>>(keys, vals, src_keys, src_vals, off, list, ctrl, single_n,
@@ -61,8 +47,8 @@ rs_status launch_warp_bits(uint32_t* keys, uint32_t* vals, const uint32_t* src_k
                            uint32_t grid, uint32_t key_type, cudaStream_t stream) {
     using L = WarpSortSmem<WARP_SORT_ITEMS, BITS, PAIRS>;
     auto kern = k_warp_sort<WARP_SORT_ITEMS, BITS, PAIRS>;
-    static uint64_t attr_on = 0;
-    rs_status st = allow_smem(kern, L::BYTES, &attr_on);
+    static DeviceOnce smem_set;
+    rs_status st = allow_smem_once(kern, L::BYTES, smem_set);
     if (st != RS_OK) return st;
     note_launch_begin(KK_WARP, stream);
     kern<<<grid, WARP_SORT_THREADS, L::BYTES, stream>>>(keys, vals, src_keys, src_vals, off, list,

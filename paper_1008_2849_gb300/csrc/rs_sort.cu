@@ -61,16 +61,9 @@ static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, v
         constexpr int T = 1024;
         constexpr size_t SMEM = HIST_COL_WORDS * sizeof(uint32_t);
         auto kern = key_type != KEY_U32 ? k_hist4_cols<T, true> : k_hist4_cols<T, false>;
-        static uint64_t attr_on[2] = {0, 0};  // per instance, one bit per device
-        uint64_t& on = attr_on[key_type != KEY_U32 ? 1 : 0];
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return RS_ERR_CUDA;
-        if (!((on >> dev) & 1u)) {
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM) != cudaSuccess)
-                return RS_ERR_CUDA;
-            on |= 1ull << dev;
-        }
+        static DeviceOnce smem_set[2];  // per instance
+        st = allow_smem_once(kern, SMEM, smem_set[key_type != KEY_U32 ? 1 : 0]);
+        if (st != RS_OK) return st;
         uint32_t grid = (uint32_t)di.sm_count;
         const uint32_t need = (vec4 + T - 1) / T;
         if (grid > need) grid = need > 0 ? need : 1;
