@@ -256,8 +256,8 @@ typedef enum rs_tune_knob {
     RS_TUNE_SMALL_MAX = 4,        /* arrays and segments up to this size (<= 8192) take the
                                      one-CTA shared-memory sort; segments up to 4096 always do */
     RS_TUNE_TILE_SEG = 5,         /* tile shape index of the segmented scatter passes */
-    RS_TUNE_WARP_MAX = 6,         /* arrays and segments up to this size (<= 512) take the
-                                     one-warp shared-memory sort; 0 or 1 turns it off */
+    RS_TUNE_WARP_MAX = 6,         /* segments (and MSD-first buckets) up to this size (<= 512)
+                                     take the one-warp shared-memory sort; 0 turns it off */
     RS_TUNE_SMALL_BITS = 7,       /* digit width of the one-warp and one-CTA sorts: 8 (four
                                      passes, the default) or 4 (eight passes) */
     RS_TUNE_MSD = 8               /* 1: unsigned whole arrays of up to 2^21 items may take the

@@ -8,8 +8,8 @@ under every candidate setting and keeps the fastest:
 * whole arrays: the tile shape of the scatter passes, for key-value and for
   keys-only sorts; up to 2^21 items, the MSD-first order of Alg. 2 (one pass
   by the top digit, then on-chip bucket sorts) or the four LSD passes; for
-  arrays up to 8192 items, which take the one-warp sort
-  (up to 512 items) and the one-CTA sort, and at which digit width;
+  arrays up to 8192 items, which take the one-CTA sort, and at which digit
+  width;
 * segmented batches: the tile shape of the segmented scatter passes and the
   largest segment sorted by the one-CTA sort (4096 or 8192); for batches of
   short arrays the largest segment sorted by the one-warp sort and the digit
@@ -111,39 +111,37 @@ def tune_whole(rs, torch, inputs, reps=3, quick=False):
 
 
 def tune_one_cta(rs, torch, inputs, reps=3):
-    """Class 0 (up to 2^13 items): which arrays take the one-warp sort
-    (warp_max 0 or 512) and the one-CTA sort (small_max 4096 or 8192), and the
-    digit width of both (4 or 8 bits), timed at 512 and at 8192 pairs; the
-    score of a setting is the sum of its two times over the best ones."""
+    """Class 0 (up to 2^13 items): which whole arrays take the one-CTA sort
+    (small_max 4096 or 8192; larger ones the scatter passes) and its digit
+    width (4 or 8 bits), timed at 512 and at 8192 pairs; the score of a
+    setting is the sum of its two times over the best ones."""
     cases = {}
     for n in (512, 8192):
         k = torch.from_numpy(inputs.keys("uniform", n, seed=300).view(np.int32)).cuda()
         v = torch.arange(n, dtype=torch.int32, device="cuda")
         cases[n] = (k, v, torch.empty_like(k), torch.empty_like(v))
-    names = ("warp_max", "small_max", "small_bits")
+    names = ("small_max", "small_bits")
     old = {k: rs.tune_get_class(0, k) for k in names}
     res = {}
-    for warp_max in (0, 512):
-        for small in (4096, 8192):
-            for bits in (4, 8):
-                for name, val in zip(names, (warp_max, small, bits)):
-                    rs.tune_set_class(0, name, val)
-                times = []
-                for n, (k, v, kb, vb) in cases.items():
-                    def restore():
-                        kb.copy_(k)
-                        vb.copy_(v)
-                    g = rs.Graph(kb, vb)
-                    times.append(_time_graph(rs, torch, g, restore, reps))
-                    g.close()
-                res["%d/%d/%d" % (warp_max, small, bits)] = times
+    for small in (4096, 8192):
+        for bits in (4, 8):
+            for name, val in zip(names, (small, bits)):
+                rs.tune_set_class(0, name, val)
+            times = []
+            for n, (k, v, kb, vb) in cases.items():
+                def restore():
+                    kb.copy_(k)
+                    vb.copy_(v)
+                g = rs.Graph(kb, vb)
+                times.append(_time_graph(rs, torch, g, restore, reps))
+                g.close()
+            res["%d/%d" % (small, bits)] = times
     for name, val in old.items():
         rs.tune_set_class(0, name, val)
     best_t = [min(t[i] for t in res.values()) for i in range(2)]
     best = min(res, key=lambda c: sum(res[c][i] / best_t[i] for i in range(2)))
-    warp_max, small, bits = (int(x) for x in best.split("/"))
-    return {"0": {"warp_max": warp_max, "small_max": small, "small_bits": bits,
-                  "one_chip_ms": res}}
+    small, bits = (int(x) for x in best.split("/"))
+    return {"0": {"small_max": small, "small_bits": bits, "one_cta_ms": res}}
 
 
 def tune_tiny_segments(rs, torch, inputs, reps=3):

@@ -159,7 +159,7 @@ Knobs& knobs() {
     // {tile_pairs, tile_keys, tile_seg, small_max, warp_max, small_bits, msd}.
     // The MSD-first order measured faster only up to 2^16 items (class 1).
     static Knobs k{{{1, 1, 3, 8192, 512, 8, 0}, {1, 1, 3, 4096, 512, 8, 1},
-                    {1, 1, 3, 4096, 512, 8, 0}, {3, 3, 3, 4096, 512, 8, 0},
+                    {1, 3, 3, 4096, 512, 8, 0}, {3, 3, 3, 4096, 512, 8, 0},
                     {3, 3, 3, 4096, 512, 8, 0}, {3, 3, 3, 4096, 512, 8, 0}},
                    kDefaultSpinLimit, 0, 4, 3};
     return k;

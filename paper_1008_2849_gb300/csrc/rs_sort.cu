@@ -112,9 +112,8 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     rs_status st = device_info(&di);
     if (st != RS_OK) return st;
     const ClassKnobs& ck = knobs().cls[size_class(n)];
-    if (n <= (uint32_t)ck.warp_max && n <= warp_sort_capacity())
-        return launch_warp_sort(keys, vals, nullptr, nullptr, nullptr, n, ck.small_bits, key_type,
-                                stream);
+    // A single small array takes one CTA (one warp alone measured slower);
+    // the one-warp sort serves batches of short segments and MSD buckets.
     if (n <= (uint32_t)ck.small_max && n <= small_sort_capacity())
         return launch_small_sort(keys, vals, nullptr, nullptr, nullptr, n, n, ck.small_bits,
                                  key_type, stream);
