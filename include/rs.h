@@ -1,7 +1,8 @@
 /*
  * rs.h -- C ABI of librs.so: stable ascending LSD radix sort of 32-bit
  * unsigned keys, optionally carrying 32-bit values, on one NVIDIA GB300
- * (sm_103a).
+ * (sm_103a); also signed and IEEE-float 32-bit keys (rs_sort_typed_ex),
+ * 64-bit keys (rs_sort64_ex), segmented batches and captured graphs.
  *
  * The operation is the one stated by Wassenberg & Sanders, "Faster Radix
  * Sort via Virtual Memory and Write-Combining" (2010): 32-bit integer keys,
@@ -20,7 +21,8 @@
  *    otherwise GPU-addressable), owned by the caller and never freed here.
  *    Pointers named h_* are HOST pointers (pinned memory gives full link
  *    bandwidth; pageable memory works but is slower).
- *  - Arrays are dense uint32_t, 4-byte aligned; no other alignment is needed.
+ *  - Arrays are dense uint32_t, 4-byte aligned (64-bit keys: uint64_t, 8-byte
+ *    aligned); no other alignment is needed.
  *    Keys and values must not overlap each other or the workspace.
  *  - Sorting is in place: the sorted keys (and values) replace the input.
  *  - n counts items (keys), 0 <= n < 2^32.  n = 0 is a no-op returning RS_OK.
