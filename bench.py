@@ -133,6 +133,22 @@ def link_bandwidths(host_buf, dev, reps: int = 3):
     return out[0], out[1]
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model as /proc/cpuinfo names it (best effort)."""
+    try:
+        fields = {}
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                key, val = line.split(":", 1)
+                fields.setdefault(key.strip(), val.strip())
+        if "model name" in fields:
+            return fields["model name"]
+        return "implementer %s part %s" % (fields.get("CPU implementer", "?"),
+                                           fields.get("CPU part", "?"))
+    except OSError:
+        return "unknown"
+
+
 def cpu_oracle_rate(seconds_budget: float = 12.0, n_sample: int = 1 << 25):
     """Time the CPU oracle (threaded, all host cores) on a bounded sample of
     the workload: 2^25 uniform pairs (seed 2), value = index."""
@@ -150,9 +166,17 @@ def cpu_oracle_rate(seconds_budget: float = 12.0, n_sample: int = 1 << 25):
         rates.append(n_sample / dt)
         if time.perf_counter() - t_start > seconds_budget or len(rates) >= 5:
             break
+    # The plain single-threaded oracle on a smaller bounded sample, for scale.
+    n_one = 1 << 23
+    t0 = time.perf_counter()
+    oracle.sort_pairs(k[:n_one], v[:n_one])
+    single = n_one / (time.perf_counter() - t0)
     return {"value": statistics.median(rates), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d sorts of 2^25 uniform uint32 pairs (value = index), threaded LSD "
-                      "counting-sort oracle, median" % len(rates)}
+                      "counting-sort oracle, median" % len(rates),
+            "single_thread_value": single,
+            "single_thread_sample": "one sort of 2^23 of the same pairs, plain oracle, 1 thread",
+            "cpu": host_cpu_model()}
 
 
 def run_reference(args, world, rank):
@@ -180,7 +204,8 @@ def run_reference(args, world, rank):
                    "values": "index", "reference_sample_n": n_sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "each step sorts 2^%d of the workload's pairs on the host "
-                                   "(threaded LSD counting-sort oracle)" % args.reference_sample_log2},
+                                   "(threaded LSD counting-sort oracle)" % args.reference_sample_log2,
+                         "cpu": host_cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
