@@ -15,10 +15,13 @@ namespace rs {
 // ---------------------------------------------------------------------------
 // Shared-memory plan of k_onesweep (offsets in 32-bit words; KW = words per
 // key, 1 for 32-bit keys and 2 for 64-bit keys):
-//   in_k[2][TILE]        input keys of the current and the next tile; the
+//   in_k[2][TILE + pad]  input keys of the current and the next tile; the
 //                        current tile's values are staged here once its keys
 //                        are ranked
-//   in_v[TILE]           input values of the current tile (key-value sorts)
+//   in_v[TILE + pad]     input values of the current tile (key-value sorts)
+// An input buffer holds its tile at the same offset modulo 16 bytes as in
+// global memory (a skew of up to 12 bytes, hence the 16-byte pad), so that
+// the tile's 16-byte-aligned middle always arrives by one bulk copy.
 //   stage[TILE]          the current tile's keys in bucket order
 //   wcnt[WARPS][RADIX]   per-warp digit counts of a tile, turned into per-warp
 //                        tile positions while the tile is ranked
@@ -28,12 +31,14 @@ template <int THREADS, int ITEMS, bool PAIRS, int KW = 1>
 struct OnesweepSmem {
     static constexpr uint32_t WARPS = THREADS / 32;
     static constexpr uint32_t TILE = THREADS * ITEMS;
+    static constexpr uint32_t PAD = 4;                   // words after every input buffer
+    static constexpr uint32_t KBUF = TILE * KW + PAD;    // words per key buffer
     static constexpr uint32_t IN_K = 0;
-    static constexpr uint32_t IN_V = IN_K + 2 * TILE * KW;
-    static constexpr uint32_t STG = IN_V + (PAIRS ? TILE : 0);
+    static constexpr uint32_t IN_V = IN_K + 2 * KBUF;
+    static constexpr uint32_t STG = IN_V + (PAIRS ? TILE + PAD : 0);
     static constexpr uint32_t WCNT = STG + TILE * KW;
-    static_assert(KW == 1 || ((TILE * KW) % 4 == 0 && STG % KW == 0),
-                  "key buffers 16-byte aligned for the bulk copies, stage aligned to keys");
+    static_assert(KBUF % 4 == 0 && (TILE + PAD) % 4 == 0 && STG % KW == 0,
+                  "input buffers 16-byte aligned for the bulk copies, stage aligned to keys");
     static constexpr uint32_t MASK = WCNT + WARPS * RADIX;
     static constexpr uint32_t WORDS = MASK + WARPS * RADIX;
     static constexpr size_t BYTES = WORDS * sizeof(uint32_t);
@@ -130,7 +135,8 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
     extern __shared__ uint4 s_dyn[];
     uint32_t* const smem = reinterpret_cast<uint32_t*>(s_dyn);
     K* const s_stage = reinterpret_cast<K*>(smem + L::STG);
-    K* const s_keys = reinterpret_cast<K*>(smem + L::IN_K);  // [2][TILE]
+    // Key buffer b (as K*), not yet skewed.
+    auto key_buf = [&](uint32_t b) { return reinterpret_cast<K*>(smem + L::IN_K + b * L::KBUF); };
     uint32_t* const s_wcnt = smem + L::WCNT;
     const uint32_t* const s_in_v = smem + L::IN_V;
     __shared__ uint32_t s_gbase[RADIX];  // G[pass][b]
@@ -200,27 +206,37 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
     }
     __syncthreads();
 
-    // Start copying the g.y items from src + g.x into dst (collective): the
-    // 16-byte-aligned middle by one bulk copy, the few items before and after
-    // it by per-thread copies, all completing on `bar`.  Items are keys (K)
-    // or values (32-bit).
+    // Skew of a tile in its input buffer: the items from the 16-byte
+    // boundary at or before the tile's first item in global memory.
+    auto skew_of = [](const auto* src, uint4 g) -> uint32_t {
+        using T = std::remove_cv_t<std::remove_pointer_t<decltype(src)>>;
+        return (uint32_t)(((uintptr_t)(src + g.x) & 15u) / sizeof(T));
+    };
+    // Start copying the g.y items from src + g.x into buffer dst at the
+    // tile's skew (collective): the 16-byte-aligned middle by one bulk copy,
+    // the few items before and after it by per-thread copies, all completing
+    // on `bar`.  Items are keys (K) or values (32-bit).
     auto issue_copy = [&](auto* dst, const auto* src, uint4 g, uint64_t* bar) {
         using T = std::remove_cv_t<std::remove_pointer_t<decltype(src)>>;
         constexpr uint32_t PER16 = 16 / sizeof(T);  // items per 16 bytes
         const uint32_t valid = g.y;
         const T* from = src + g.x;
-        // Items before the first 16-byte boundary of the source; the bulk copy
-        // needs the same alignment on both sides, so it is used only when the
-        // destination offset agrees.
-        const uint32_t head = (uint32_t)((16u - ((uintptr_t)from & 15u)) & 15u) / sizeof(T);
-        const bool bulk_ok = head == 0 && valid >= PER16;
-        const uint32_t nb = bulk_ok ? (valid & ~(PER16 - 1)) : 0u;
+        T* to = dst + skew_of(src, g);  // item i lands at to[i]: same offset mod 16 B
+        const uint32_t a0 = (PER16 - skew_of(src, g)) & (PER16 - 1);  // first aligned item
+        const uint32_t nb = valid > a0 ? ((valid - a0) & ~(PER16 - 1)) : 0u;
+        const uint32_t head = nb ? a0 : valid;  // items copied one by one: [0, head) and
+        const uint32_t tail = a0 + nb;          // [tail, valid) when there is a bulk part
         if (nb < valid) {  // CTA-uniform
             bool issued = false;
-            for (uint32_t i = nb + tid; i < valid; i += THREADS) {
-                cp_async_elem(dst + i, from + i);
+            for (uint32_t i = tid; i < head; i += THREADS) {
+                cp_async_elem(to + i, from + i);
                 issued = true;
             }
+            if (nb)
+                for (uint32_t i = tail + tid; i < valid; i += THREADS) {
+                    cp_async_elem(to + i, from + i);
+                    issued = true;
+                }
             if (issued) cp_async_mbar_arrive(bar);
             __syncthreads();  // every pending count is raised before the arrival below
         }
@@ -229,7 +245,7 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
             // before the bulk copy's writes.
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, nb * (uint32_t)sizeof(T));
-            if (nb) tma_load_1d(dst, from, nb * (uint32_t)sizeof(T), bar);
+            if (nb) tma_load_1d(to + a0, from + a0, nb * (uint32_t)sizeof(T), bar);
         }
     };
 
@@ -260,9 +276,10 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
         }
     };
     const uint32_t wofs = warp * WARP_ITEMS;
-    // Count the slots of warp w of the tile in key buffer b into wcnt row w.
-    auto count_slots_of = [&](uint32_t b, uint32_t valid, uint32_t w) {
-        const K* keys = s_keys + b * TILE + w * WARP_ITEMS + lane;
+    // Count the slots of warp w of tile g (in key buffer b) into wcnt row w.
+    auto count_slots_of = [&](uint32_t b, uint4 g, uint32_t w) {
+        const uint32_t valid = g.y;
+        const K* keys = key_buf(b) + skew_of(src_k, g) + w * WARP_ITEMS + lane;
         uint32_t* row = s_wcnt + w * RADIX;
         if (valid == TILE) {
 #pragma unroll
@@ -320,10 +337,10 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
     // Prologue: the first tile's data and counts; the second tile's id is taken
     // once they are published.
     if (s_ids[0] >= num_tiles) return;
-    issue_copy(s_keys, src_k, s_geo[0], &s_bar[0]);
+    issue_copy(key_buf(0), src_k, s_geo[0], &s_bar[0]);
     if (PAIRS) issue_copy(smem + L::IN_V, src_v, s_geo[0], &s_bar[2]);
     wait_bar(0);
-    count_slots_of(0, s_geo[0].y, warp);
+    count_slots_of(0, s_geo[0], warp);
     __syncthreads();
     if (tid < RADIX) prep_tile(s_ids[0], s_geo[0].z);
     if (tid == 0) {
@@ -342,7 +359,7 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
         const uint4 geo = s_geo[it & 3];
         const uint4 ngeo = s_geo[(it + 1) & 3];
         const bool have_next = nxt < num_tiles;
-        if (have_next) issue_copy(s_keys + (buf ^ 1) * TILE, src_k, ngeo, &s_bar[buf ^ 1]);
+        if (have_next) issue_copy(key_buf(buf ^ 1), src_k, ngeo, &s_bar[buf ^ 1]);
         // Segmented: this tile's bucket bases, fetched now, used after ranking.
         uint32_t seg_base = 0;
         if (SEG && tid < RADIX) seg_base = seg_gofs[((size_t)geo.w * PASSES + pass) * RADIX + tid];
@@ -353,7 +370,8 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
 
         const uint32_t valid = geo.y;
         const uint32_t first_tile = geo.z;  // look-back stops here
-        K* const in_k = s_keys + buf * TILE;
+        K* const in_k = key_buf(buf) + skew_of(src_k, geo);
+        const uint32_t* const in_v = s_in_v + (PAIRS ? skew_of(src_v, geo) : 0u);
         uint32_t* const in_kv = reinterpret_cast<uint32_t*>(in_k);  // staged values
 
         // ---- 2. rank, and stage the keys ------------------------------------
@@ -471,18 +489,17 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
             }
         }
         if (have_next) {
-            const uint32_t nvalid = ngeo.y;
             if (SPARE) {
                 if (warp >= LB_WARPS) {
                     wait_bar(buf ^ 1);
                     for (uint32_t w = warp - LB_WARPS; w < WARPS; w += WARPS - LB_WARPS)
-                        count_slots_of(buf ^ 1, nvalid, w);
+                        count_slots_of(buf ^ 1, ngeo, w);
                 } else {
                     phase ^= 1u << (buf ^ 1);  // the count warps waited for it
                 }
             } else {
                 wait_bar(buf ^ 1);
-                count_slots_of(buf ^ 1, nvalid, warp);
+                count_slots_of(buf ^ 1, ngeo, warp);
             }
         }
         // Every thread stages its own items' values (the key buffer is free).
@@ -490,7 +507,7 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
             wait_bar(2);
             uint32_t vv[ITEMS];
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j) vv[j] = s_in_v[wofs + j * 32 + lane];
+            for (int j = 0; j < ITEMS; ++j) vv[j] = in_v[wofs + j * 32 + lane];
             if (valid == TILE) {
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) in_kv[pos[j]] = vv[j];

@@ -8,7 +8,6 @@ namespace rs {
 namespace {
 
 constexpr uint32_t kMinLargeSegment = 4097;  // segments up to 4096 items always take the one-CTA sort
-constexpr int SEG_HIST_THREADS = 512;
 
 }  // namespace
 
@@ -98,9 +97,16 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
 
     // Large segments: histograms, bucket bases, four scatter passes.
     note_launch_begin(KK_SEG_HIST, stream);
-    k_seg_hist<SEG_HIST_THREADS><<<di.sm_count * 2, SEG_HIST_THREADS, 0, stream>>>(
-        keys, ctrl, tile_geo, gofs, static_cast<uint4*>(status[0]),
-        (uint32_t)((L.status1 - L.status0) / sizeof(uint4)), key_type);
+    {
+        constexpr size_t SMEM = SEG_HIST_COL_WORDS * sizeof(uint32_t);
+        auto kern = key_type != KEY_U32 ? k_seg_hist<true> : k_seg_hist<false>;
+        static DeviceOnce smem_set[2];
+        st = allow_smem_once(kern, SMEM, smem_set[key_type != KEY_U32 ? 1 : 0]);
+        if (st != RS_OK) return st;
+        kern<<<di.sm_count, SEG_HIST_THREADS, SMEM, stream>>>(
+            keys, ctrl, tile_geo, gofs, static_cast<uint4*>(status[0]),
+            (uint32_t)((L.status1 - L.status0) / sizeof(uint4)), key_type);
+    }
     note_launch_end(KK_SEG_HIST, stream);
     note_launch_begin(KK_SEG_SCAN, stream);
     k_seg_scan<<<di.sm_count * 2, 1024, 0, stream>>>(ctrl, gofs, large_first);

@@ -110,55 +110,107 @@ k_seg_plan(const uint32_t* __restrict__ off, uint32_t num_segments, uint32_t n, 
 
 // ---------------------------------------------------------------------------
 // k_seg_hist: digit histograms of every large segment, added into
-// hist[ordinal][4][256] (zeroed by the caller).  CTA c takes a contiguous run
-// of tiles, so consecutive tiles mostly share a segment: counts accumulate in
-// shared memory and are added to global memory only when the segment changes.
-// Also clears the first scatter pass's status array.
+// hist[ordinal][4][256] (zeroed by the caller).  One CTA of 1024 threads per
+// SM takes a contiguous run of tiles, so consecutive tiles mostly share a
+// segment.  Counts accumulate in per-lane shared-memory columns (bin b of
+// digit p as seen by lane l at word (p*256 + b)*32 + l: the 32 lanes of a warp
+// always add into 32 different banks) and are summed into global memory only
+// when the segment changes.  Also clears the first scatter pass's status
+// array.  TYPED: keys are mapped onto their ordered words first.
 // ---------------------------------------------------------------------------
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
+constexpr uint32_t SEG_HIST_THREADS = 1024;
+constexpr uint32_t SEG_HIST_COL_WORDS = PASSES * RADIX * 32;
+constexpr uint32_t SEG_HIST_GEO_CHUNK = 1024;  // tile geometries staged at a time
+
+template <bool TYPED>
+__global__ void __launch_bounds__(SEG_HIST_THREADS, 1)
 k_seg_hist(const uint32_t* __restrict__ keys, const Ctrl* __restrict__ ctrl,
            const uint4* __restrict__ tile_geo, uint32_t* __restrict__ hist,
            uint4* __restrict__ clear, uint32_t clear_vec4, uint32_t key_type) {
-    __shared__ uint32_t s_h[PASSES * RADIX];
-    const uint32_t tid = threadIdx.x;
-    for (uint32_t i = blockIdx.x * THREADS + tid; i < clear_vec4; i += gridDim.x * THREADS)
+    extern __shared__ uint4 s_cols4[];
+    uint32_t* const s_col = reinterpret_cast<uint32_t*>(s_cols4);
+    constexpr uint32_t T = SEG_HIST_THREADS;
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    for (uint32_t i = blockIdx.x * T + tid; i < clear_vec4; i += gridDim.x * T)
         clear[i] = make_uint4(0, 0, 0, 0);
     if (ctrl->err != 0) return;
     const uint32_t tiles = ctrl->seg_tiles;
     const uint32_t per = (tiles + gridDim.x - 1) / gridDim.x;
     const uint32_t t_lo = blockIdx.x * per;
     const uint32_t t_hi = t_lo + per < tiles ? t_lo + per : tiles;
-    for (uint32_t i = tid; i < PASSES * RADIX; i += THREADS) s_h[i] = 0;
+    if (t_lo >= t_hi) return;
+    for (uint32_t i = tid; i < SEG_HIST_COL_WORDS / 4; i += T) s_cols4[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    uint32_t cur = 0xffffffffu;
-    for (uint32_t t = t_lo; t < t_hi; ++t) {
-        const uint4 g = tile_geo[t];
-        if (g.w != cur) {
-            if (cur != 0xffffffffu) {
-                __syncthreads();
-                for (uint32_t i = tid; i < PASSES * RADIX; i += THREADS) {
-                    const uint32_t c = s_h[i];
-                    if (c) atomicAdd(hist + (size_t)cur * PASSES * RADIX + i, c);
-                    s_h[i] = 0;
-                }
-                __syncthreads();
-            }
-            cur = g.w;
-        }
-        for (uint32_t i = tid; i < g.y; i += THREADS) {
-            const uint32_t k = key_to_ordered(ld_stream(keys + g.x + i), key_type);
+    uint32_t* const mycol = s_col + lane;
+    auto count_key = [&](uint32_t k) {
+        if (TYPED) k = key_to_ordered(k, key_type);
 #pragma unroll
-            for (uint32_t p = 0; p < PASSES; ++p)
-                atomicAdd(&s_h[p * RADIX + ((k >> (p * RADIX_BITS)) & (RADIX - 1))], 1u);
+        for (uint32_t p = 0; p < PASSES; ++p)
+            atomicAdd(mycol + ((p * RADIX + ((k >> (p * RADIX_BITS)) & (RADIX - 1))) << 5), 1u);
+    };
+    // Thread `bin` sums (and clears) the 32 columns of one bin, in rotated
+    // order so that a warp's reads fall into 32 different banks.
+    auto flush = [&](uint32_t seg) {
+        __syncthreads();
+        for (uint32_t bin = tid; bin < PASSES * RADIX; bin += T) {
+            uint32_t c = 0;
+#pragma unroll 8
+            for (uint32_t j = 0; j < 32; ++j) {
+                const uint32_t w = (bin << 5) + ((j + bin) & 31);
+                c += s_col[w];
+                s_col[w] = 0;
+            }
+            if (c) atomicAdd(hist + (size_t)seg * PASSES * RADIX + bin, c);
+        }
+        __syncthreads();
+    };
+    // Counts the keys [lo, hi): up to 3 before the first 16-byte boundary
+    // and up to 3 after the last one one by one, the rest as 16-byte
+    // vectors, two in flight per thread.
+    auto count_range = [&](uint32_t lo, uint32_t hi) {
+        const uint32_t* src = keys + lo;
+        const uint32_t m = hi - lo;
+        uint32_t head = (uint32_t)(((16u - ((uintptr_t)src & 15u)) & 15u) >> 2);
+        if (head > m) head = m;
+        const uint32_t nvec = (m - head) >> 2;
+        const uint4* body = reinterpret_cast<const uint4*>(src + head);
+        uint32_t v = tid;
+        for (; v + T < nvec; v += 2 * T) {
+            const uint4 x = ld_stream(body + v), y = ld_stream(body + v + T);
+            count_key(x.x); count_key(x.y); count_key(x.z); count_key(x.w);
+            count_key(y.x); count_key(y.y); count_key(y.z); count_key(y.w);
+        }
+        if (v < nvec) {
+            const uint4 x = ld_stream(body + v);
+            count_key(x.x); count_key(x.y); count_key(x.z); count_key(x.w);
+        }
+        const uint32_t tail = head + nvec * 4;
+        if (tid < head) count_key(ld_stream(src + tid));
+        if (tid < 4 && tail + tid < m) count_key(ld_stream(src + tail + tid));
+    };
+    // The CTA's tiles, a chunk of geometries at a time in shared memory.
+    // Consecutive tiles of one segment cover consecutive keys, so every run
+    // of them is counted as one range (no per-tile wait on its geometry).
+    __shared__ uint4 s_g[SEG_HIST_GEO_CHUNK];
+    uint32_t cur = 0xffffffffu;
+    for (uint32_t c0 = t_lo; c0 < t_hi; c0 += SEG_HIST_GEO_CHUNK) {
+        const uint32_t cn = t_hi - c0 < SEG_HIST_GEO_CHUNK ? t_hi - c0 : SEG_HIST_GEO_CHUNK;
+        __syncthreads();  // the previous chunk is no longer read
+        for (uint32_t i = tid; i < cn; i += T) s_g[i] = tile_geo[c0 + i];
+        __syncthreads();
+        for (uint32_t ra = 0; ra < cn;) {
+            const uint32_t seg = s_g[ra].w;
+            uint32_t rb = ra;
+            while (rb + 1 < cn && s_g[rb + 1].w == seg) ++rb;
+            if (seg != cur) {
+                if (cur != 0xffffffffu) flush(cur);
+                cur = seg;
+            }
+            count_range(s_g[ra].x, s_g[rb].x + s_g[rb].y);
+            ra = rb + 1;
         }
     }
-    __syncthreads();
-    if (cur != 0xffffffffu)
-        for (uint32_t i = tid; i < PASSES * RADIX; i += THREADS) {
-            const uint32_t c = s_h[i];
-            if (c) atomicAdd(hist + (size_t)cur * PASSES * RADIX + i, c);
-        }
+    flush(cur);
 }
 
 // ---------------------------------------------------------------------------
