@@ -89,10 +89,15 @@ def measured_peaks():
 
 
 def source_hash(paths) -> str:
+    """Hash of the code in `paths`: line comments, trailing blanks and blank
+    lines are left out, so that editing a comment keeps the hash."""
     h = hashlib.sha256()
     for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

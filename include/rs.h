@@ -256,7 +256,8 @@ typedef enum rs_tune_knob {
     RS_TUNE_HIST_MODE = 3,        /* 0: lane atomics, 1: lane-0 group + atomics, 2: ballot groups,
                                      3: one private shared column per lane (default) */
     RS_TUNE_SMALL_MAX = 4,        /* arrays and segments up to this size (<= 8192) take the
-                                     one-CTA shared-memory sort; segments up to 4096 always do */
+                                     one-CTA shared-memory sort; segments up to 4096 always
+                                     take an on-chip sort */
     RS_TUNE_TILE_SEG = 5,         /* tile shape index of the segmented scatter passes */
     RS_TUNE_WARP_MAX = 6,         /* segments (and MSD-first buckets) up to this size (<= 512)
                                      take the one-warp shared-memory sort; 0 turns it off */

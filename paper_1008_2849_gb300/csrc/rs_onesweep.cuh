@@ -54,10 +54,12 @@ struct OnesweepSmem {
 // order per CTA): while tile i is ranked, the keys of tile i+1 are already
 // being copied into the other key buffer by the tensor memory accelerator
 // (one bulk copy, completing on an mbarrier); tile i+1's values follow as soon
-// as tile i's values have been staged.  A base that is not 16-byte aligned, or
-// a ragged last tile, falls back to per-thread 4-byte asynchronous copies on
+// as tile i's values have been staged.  A tile sits in its buffer at its
+// global 16-byte phase, so the bulk copy takes its aligned middle and at most
+// three items before and after it arrive by per-thread asynchronous copies on
 // the same barrier.  As soon as tile i+1's keys have landed its per-warp digit
-// counts are taken and its tile counts published.
+// counts are taken and its tile counts published.  Keys are 32-bit (K =
+// uint32_t) or 64-bit (K = unsigned long long, eight passes); values 32-bit.
 //
 // Item order: warp w owns tile items [w*32*ITEMS, (w+1)*32*ITEMS); its item j
 // on lane l is tile item w*32*ITEMS + j*32 + l, so the (warp, j, lane) order
@@ -79,7 +81,8 @@ struct OnesweepSmem {
 //     before this one at once, add AGG counts from the nearest one on until an
 //     INC prefix, re-reading from the first tile that has not published yet;
 //     publish this tile's inclusive prefix (INC).  Meanwhile the other warps
-//     count the next tile, whose counts are published right after.  A CTA takes
+//     count the next tile; its counts are published while this tile is
+//     stored.  A CTA takes
 //     its next tile id only after its look-back, so between taking an id and
 //     publishing that tile's counts it waits on no other CTA; every tile before
 //     this one has therefore published its counts or will without waiting, and
@@ -90,7 +93,9 @@ struct OnesweepSmem {
 //  5. Slot s of the staging buffer is stored to
 //       dst[G[b] + prefix_before_this_tile[b] + (s - tile_excl[b])],
 //     so consecutive threads store consecutive addresses of one bucket run.
-//     Every global store is checked against n (ERR_BOUNDS instead of a fault).
+//     Threads >= 256 start with a larger share of the slots while threads <
+//     256 prepare the next tile (its counts, AGG and warp bases).  Every
+//     global store is checked against n (ERR_BOUNDS instead of a fault).
 // ---------------------------------------------------------------------------
 // Typed keys (TYPED): the first pass that moves data maps every key it reads
 // onto its ordered unsigned word (key_to_ordered), so all digits, ranks and
