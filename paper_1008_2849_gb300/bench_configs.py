@@ -115,6 +115,17 @@ def main(argv=None) -> int:
         del k, v, kb, vb, ws
     out["pairs_mid_sizes_lsd_vs_msd_first"] = mid
 
+    # Keys only at 2^27 (uniform, seed 3): 8 B per key per pass.
+    n = 1 << 27
+    k = torch.from_numpy(inputs.keys("uniform", n, seed=3).view(np.int32)).cuda()
+    kb = torch.empty_like(k)
+    ws = rs.alloc_workspace(n, False)
+    ms = _timed(torch, stream, lambda: rs.sort_keys_ex(kb, ws, stream), lambda: kb.copy_(k),
+                a.steps, a.warmup)
+    rs.check_stream()
+    out["keys_2^27_uniform"] = {"ms": ms, "keys_per_s": n / (ms / 1e3)}
+    del k, kb, ws
+
     # 2. distribution sweep, 2^27 pairs
     n = 1 << 27
     v = torch.arange(n, dtype=torch.int32, device="cuda")

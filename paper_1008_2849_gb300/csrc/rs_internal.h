@@ -43,7 +43,8 @@ void note_launch_end(int kind, cudaStream_t stream);
     X(2, 256, 16, 2, 32)    \
     X(3, 384, 13, 2, 8)     \
     X(4, 384, 12, 2, 8)     \
-    X(5, 1024, 8, 1, 32)
+    X(5, 1024, 8, 1, 32)    \
+    X(6, 384, 18, 2, 8)
 
 struct TileConfig {
     int threads;
