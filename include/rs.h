@@ -2,7 +2,8 @@
  * rs.h -- C ABI of librs.so: stable ascending LSD radix sort of 32-bit
  * unsigned keys, optionally carrying 32-bit values, on one NVIDIA GB300
  * (sm_103a); also signed and IEEE-float 32-bit keys (rs_sort_typed_ex),
- * 64-bit keys (rs_sort64_ex), segmented batches and captured graphs.
+ * 64-bit keys and 64-bit values (rs_sort_kv_ex, rs_sort64_ex), segmented
+ * batches and captured graphs.
  *
  * The operation is the one stated by Wassenberg & Sanders, "Faster Radix
  * Sort via Virtual Memory and Write-Combining" (2010): 32-bit integer keys,
@@ -21,8 +22,8 @@
  *    otherwise GPU-addressable), owned by the caller and never freed here.
  *    Pointers named h_* are HOST pointers (pinned memory gives full link
  *    bandwidth; pageable memory works but is slower).
- *  - Arrays are dense uint32_t, 4-byte aligned (64-bit keys: uint64_t, 8-byte
- *    aligned); no other alignment is needed.
+ *  - Arrays are dense uint32_t, 4-byte aligned (64-bit keys and values:
+ *    uint64_t, 8-byte aligned); no other alignment is needed.
  *    Keys and values must not overlap each other or the workspace.
  *  - Sorting is in place: the sorted keys (and values) replace the input.
  *  - n counts items (keys), 0 <= n < 2^32.  n = 0 is a no-op returning RS_OK.
@@ -121,8 +122,18 @@ rs_status rs_sort_pairs_segmented_ex(uint32_t* d_keys, uint32_t* d_vals, size_t 
  * caller's own bit patterns, stably sorted (equal keys keep their order).
  * d_vals may be NULL (keys only).  Otherwise as the _ex calls above, with the
  * same workspace size; the scatter passes of typed sorts always use tile
- * shape 3.  An unknown key_type is RS_ERR_INVALID_ARG. */
-typedef enum rs_key_type { RS_KEY_U32 = 0, RS_KEY_I32 = 1, RS_KEY_F32 = 2 } rs_key_type;
+ * shape 3.  These two calls take the 32-bit key types only; any other
+ * key_type is RS_ERR_INVALID_ARG.  The 64-bit types (RS_KEY_U64, RS_KEY_I64,
+ * RS_KEY_F64: unsigned, two's-complement and IEEE-754 binary64, by the same
+ * rules) are sorted by rs_sort_kv_ex below. */
+typedef enum rs_key_type {
+    RS_KEY_U32 = 0,
+    RS_KEY_I32 = 1,
+    RS_KEY_F32 = 2,
+    RS_KEY_U64 = 3,
+    RS_KEY_I64 = 4,
+    RS_KEY_F64 = 5
+} rs_key_type;
 
 rs_status rs_sort_typed_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n, int key_type,
                            void* cuda_stream, void* d_workspace, size_t workspace_bytes);
@@ -147,6 +158,29 @@ size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments);
 rs_status rs_sort64_ex(uint64_t* d_keys, uint32_t* d_vals, size_t n, void* cuda_stream,
                        void* d_workspace, size_t workspace_bytes);
 size_t rs_workspace_bytes64(size_t n, int with_values);
+
+/* Keys and values of every width this library sorts, in one call: keys of
+ * any rs_key_type (32-bit or 64-bit words, unsigned, signed or IEEE float,
+ * ordered as stated above), carrying values of value_bits = 0 (keys only;
+ * d_vals NULL), 32 or 64 bits (d_vals not NULL).  Sec. 1 fixes the paper's
+ * items at 32-bit keys with optional 32-bit values and notes that larger
+ * ones work the same way; Sec. 4 leaves K general.  64-bit keys take eight
+ * passes (K = 64, D = 8) and a value of any width moves with its key.
+ * 32-bit keys with no or 32-bit values take the calls above (same workspace
+ * size, same kernels); every other combination takes the scatter passes for
+ * every array size (no on-chip sort of small arrays, no MSD-first order).
+ * d_keys is aligned to its key width, d_vals to its value width; keys and
+ * values do not overlap; n < 2^32; workspace_bytes >=
+ * rs_workspace_bytes_kv(n, key_type, value_bits), the workspace 256-byte
+ * aligned.  Asynchronous on cuda_stream, in place, stable.  An unknown
+ * key_type or value_bits is RS_ERR_INVALID_ARG, and so are d_vals NULL with
+ * value_bits != 0 and d_vals not NULL with value_bits = 0.
+ * rs_sort64_ex(k, v, ...) is
+ * rs_sort_kv_ex(k, v, ..., RS_KEY_U64, v ? 32 : 0, ...).
+ * rs_workspace_bytes_kv returns 0 for n = 0 or unknown types. */
+rs_status rs_sort_kv_ex(void* d_keys, void* d_vals, size_t n, int key_type, int value_bits,
+                        void* cuda_stream, void* d_workspace, size_t workspace_bytes);
+size_t rs_workspace_bytes_kv(size_t n, int key_type, int value_bits);
 
 /* Synchronise cuda_stream (NULL = legacy default stream), then return and
  * clear the sticky device status word of the current device: RS_OK, or the

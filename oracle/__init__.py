@@ -22,6 +22,9 @@ Every function follows the paper's definitions:
   integer keys (by value) and of IEEE-754 binary32 keys (by the totalOrder
   predicate of IEEE 754-2008 Sec. 5.10): no paper counterpart; a plain merge
   sort with that comparison.
+* ``sort_kv`` -- keys and values of every width (Sec. 1: larger items sort
+  the same way): 32-bit or 64-bit keys, unsigned, signed or IEEE float, with
+  no, 32-bit or 64-bit values; a plain stable merge sort by the key.
 
 Every function takes an optional ``lib`` (a library bound by ``_bind``) so that
 the pin tests can also be run against deliberately mutated builds of the C
@@ -84,6 +87,11 @@ def _bind(path: str):
         lib.oracle_sort_typed_segmented.argtypes = [_u32p, _u32p, _u32p, _u32p, ctypes.c_size_t,
                                                     _u32p, ctypes.c_uint32, ctypes.c_int]
         lib.oracle_sort_typed_segmented.restype = ctypes.c_int
+    if hasattr(lib, "oracle_sort_kv"):
+        lib.oracle_sort_kv.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                       ctypes.c_int]
+        lib.oracle_sort_kv.restype = ctypes.c_int
     return lib
 
 
@@ -181,6 +189,9 @@ def sort_pairs_threaded(keys, vals, nthreads: int, lib=None):
 
 
 KEY_TYPES = {"u32": 0, "i32": 1, "f32": 2}
+# Every key type of sort_kv: (code, word dtype).
+KV_KEY_TYPES = {"u32": (0, np.uint32), "i32": (1, np.uint32), "f32": (2, np.uint32),
+                "u64": (3, np.uint64), "i64": (4, np.uint64), "f64": (5, np.uint64)}
 
 
 def sort_typed(keys, vals, key_type: str, lib=None):
@@ -228,4 +239,29 @@ def sort_pairs64(keys, vals, lib=None):
                                               _ptr(vo), keys.size)
     if rc:
         raise MemoryError("oracle_sort_pairs64 failed (%d)" % rc)
+    return ko, vo
+
+
+def sort_kv(keys, vals, key_type: str, lib=None):
+    """Stable ascending sort of keys read as ``key_type`` (one of
+    ``KV_KEY_TYPES``; bit patterns as uint32 or uint64 words), carrying
+    ``vals`` (uint32, uint64 or None) as opaque payloads; returns new
+    (keys, vals|None) arrays."""
+    code, kdt = KV_KEY_TYPES[key_type]
+    keys = np.ascontiguousarray(keys)
+    if keys.dtype != kdt:
+        raise TypeError("expected %s keys for %s, got %s" % (np.dtype(kdt), key_type, keys.dtype))
+    value_bits = 0
+    if vals is not None:
+        vals = np.ascontiguousarray(vals)
+        if vals.dtype not in (np.uint32, np.uint64) or vals.size != keys.size:
+            raise TypeError("values must be uint32 or uint64, one per key")
+        value_bits = 8 * vals.dtype.itemsize
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    rc = (lib or _load()).oracle_sort_kv(keys.ctypes.data, None if vals is None else vals.ctypes.data,
+                                         ko.ctypes.data, None if vo is None else vo.ctypes.data,
+                                         keys.size, code, value_bits)
+    if rc:
+        raise MemoryError("oracle_sort_kv failed (%d)" % rc)
     return ko, vo

@@ -35,6 +35,11 @@
  *     binary32 floats ordered by the totalOrder predicate of IEEE 754-2008
  *     Sec. 5.10.  These are a plain stable merge sort with that comparison,
  *     written from the definitions, not from any bit transformation.
+ *   - Items of every width (Sec. 1: the 32-bit items are a simplification;
+ *     larger items sort the same way): 32-bit or 64-bit keys of any of the
+ *     types above (64-bit: unsigned, two's-complement, IEEE-754 binary64 by
+ *     totalOrder) carrying no, 32-bit or 64-bit values.  Again a plain
+ *     stable merge sort with the key comparison; values are opaque bytes.
  *
  * Everything is written as plain loops, with no blocking, fusion or
  * reordering beyond the counting sort itself.
@@ -369,5 +374,78 @@ int oracle_sort_pairs64(const uint64_t* keys_in, const uint32_t* vals_in, uint64
     memcpy(keys_out, ka, n * sizeof(uint64_t));
     if (vals_in) memcpy(vals_out, va, n * sizeof(uint32_t));
     free(ka); free(kb); free(va); free(vb);
+    return 0;
+}
+
+
+/* ------------------------------------------------------------------------
+ * Keys and values of every width.  key_type 0, 1, 2: 32-bit words read as
+ * unsigned, two's-complement or IEEE-754 binary32 (as above); 3, 4, 5: the
+ * same three readings of 64-bit words (binary64 totalOrder: sign bit 63,
+ * magnitude = the other 63 bits read as one unsigned field).  value_bits 0
+ * (keys only), 32 or 64; a value is copied as opaque bytes.  Plain stable
+ * merge sort by the key comparison (ties keep input order), then keys and
+ * values are gathered in that order.  Returns 0, -1 on allocation failure,
+ * -3 on an unknown key_type or value_bits.
+ * ---------------------------------------------------------------------- */
+static int kv_less(const unsigned char* keys, size_t a, size_t b, int key_type) {
+    if (key_type <= 2) {
+        uint32_t x, y;
+        memcpy(&x, keys + 4 * a, 4);
+        memcpy(&y, keys + 4 * b, 4);
+        if (key_type == 0) return x < y;
+        return typed_less(x, y, key_type);
+    }
+    uint64_t x, y;
+    memcpy(&x, keys + 8 * a, 8);
+    memcpy(&y, keys + 8 * b, 8);
+    if (key_type == 3) return x < y;
+    if (key_type == 4) return (int64_t)x < (int64_t)y;
+    const uint64_t sx = x >> 63, sy = y >> 63;
+    const uint64_t mx = x & 0x7fffffffffffffffull, my = y & 0x7fffffffffffffffull;
+    if (sx != sy) return sx > sy;  /* negative sign first */
+    if (sx == 0) return mx < my;   /* both positive */
+    return mx > my;                /* both negative */
+}
+
+static void merge_sort_kv(const unsigned char* keys, size_t* idx, size_t* tmp, size_t lo,
+                          size_t hi, int key_type) {
+    if (hi - lo < 2) return;
+    const size_t mid = lo + (hi - lo) / 2;
+    merge_sort_kv(keys, idx, tmp, lo, mid, key_type);
+    merge_sort_kv(keys, idx, tmp, mid, hi, key_type);
+    size_t i = lo, j = mid, o = lo;
+    while (i < mid && j < hi) {
+        if (kv_less(keys, idx[j], idx[i], key_type))
+            tmp[o++] = idx[j++];
+        else
+            tmp[o++] = idx[i++];
+    }
+    while (i < mid) tmp[o++] = idx[i++];
+    while (j < hi) tmp[o++] = idx[j++];
+    memcpy(idx + lo, tmp + lo, (hi - lo) * sizeof(size_t));
+}
+
+int oracle_sort_kv(const void* keys_in, const void* vals_in, void* keys_out, void* vals_out,
+                   size_t n, int key_type, int value_bits) {
+    if (key_type < 0 || key_type > 5) return -3;
+    if (value_bits != 0 && value_bits != 32 && value_bits != 64) return -3;
+    if (n == 0) return 0;
+    const size_t kb = key_type <= 2 ? 4 : 8, vb = (size_t)value_bits / 8;
+    size_t* idx = (size_t*)malloc(n * sizeof(size_t));
+    size_t* tmp = (size_t*)malloc(n * sizeof(size_t));
+    if (!idx || !tmp) {
+        free(idx); free(tmp);
+        return -1;
+    }
+    for (size_t i = 0; i < n; ++i) idx[i] = i;
+    merge_sort_kv((const unsigned char*)keys_in, idx, tmp, 0, n, key_type);
+    for (size_t i = 0; i < n; ++i) {
+        memcpy((unsigned char*)keys_out + kb * i, (const unsigned char*)keys_in + kb * idx[i], kb);
+        if (vb)
+            memcpy((unsigned char*)vals_out + vb * i, (const unsigned char*)vals_in + vb * idx[i],
+                   vb);
+    }
+    free(idx); free(tmp);
     return 0;
 }

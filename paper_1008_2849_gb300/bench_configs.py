@@ -19,6 +19,10 @@
    signed integers and as IEEE floats (rs_sort_typed_ex).
 4. 64-bit keys with 32-bit values, 2^27 pairs of random words (seed 22),
    eight passes (rs_sort64_ex).
+5. Wide items through rs_sort_kv_ex at 2^27 items of random words (seed
+   23): 32-bit keys with 64-bit values (four passes), 64-bit keys (unsigned
+   and IEEE binary64) with 64-bit values and signed 64-bit keys alone (eight
+   passes).
 
 Prints one JSON line.
 """
@@ -189,6 +193,44 @@ def main(argv=None) -> int:
     rs.check_stream()
     out["pairs_2^27_key64_value32"] = {"ms": ms, "pairs_per_s": n / (ms / 1e3),
                                        "bytes_per_pair_per_pass": 24, "passes": 8}
+    del kb, vb, ws, raw
+
+    # 5. wide items (rs_sort_kv_ex), 2^27 items of random words (seed 23)
+    i64 = torch.arange(n, dtype=torch.int64, device="cuda")
+    wide = {}
+    for key_type, value_bits in (("u32", 64), ("u64", 64), ("f64", 64), ("i64", 0)):
+        kw = 8 if key_type.endswith("64") else 4
+        lo = inputs.splitmix32(23, n, 0)
+        if kw == 8:
+            hi = inputs.splitmix32(23, n, 1).astype(np.uint64)
+            k = torch.from_numpy(((hi << np.uint64(32)) | lo.astype(np.uint64)).view(np.int64))
+            del hi
+        else:
+            k = torch.from_numpy(lo.view(np.int32))
+        k = k.cuda()
+        del lo
+        vw = i64 if value_bits == 64 else None
+        kb = torch.empty_like(k)
+        vb = None if vw is None else torch.empty_like(vw)
+        nbytes = rs.workspace_bytes_kv(n, key_type, value_bits)
+        raw = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        ws = raw[(-raw.data_ptr()) % 256:][:nbytes]
+
+        def restore():
+            kb.copy_(k)
+            if vb is not None:
+                vb.copy_(vw)
+        ms = _timed(torch, stream, lambda: rs.sort_kv_ex(kb, vb, key_type, ws, stream), restore,
+                    a.steps, a.warmup)
+        rs.check_stream()
+        passes = 8 if kw == 8 else 4
+        per_pass = 2 * (kw + value_bits // 8)
+        wide["%s_keys_%d_bit_values" % (key_type, value_bits)] = {
+            "ms": ms, "items_per_s": n / (ms / 1e3), "passes": passes,
+            "bytes_per_item_per_pass": per_pass,
+            "scatter_tb_per_s": n * per_pass * passes / (ms / 1e3) / 1e12}
+        del k, kb, vb, ws, raw
+    out["items_2^27_wide"] = wide
     print(json.dumps(out), flush=True)
     return 0
 

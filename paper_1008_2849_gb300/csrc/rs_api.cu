@@ -339,24 +339,61 @@ size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments) {
 
 size_t rs_workspace_bytes64(size_t n, int with_values) {
     if (n == 0) return 0;
-    return layout_for64(n, with_values != 0).total;
+    return layout_wide(n, true, with_values ? 4u : 0u).total;
 }
 
 rs_status rs_sort64_ex(uint64_t* d_keys, uint32_t* d_vals, size_t n, void* cuda_stream,
                        void* d_workspace, size_t workspace_bytes) {
+    return rs_sort_kv_ex(d_keys, d_vals, n, RS_KEY_U64, d_vals != nullptr ? 32 : 0, cuda_stream,
+                         d_workspace, workspace_bytes);
+}
+
+namespace {
+
+bool valid_kv_types(int key_type, int value_bits) {
+    return key_type >= RS_KEY_U32 && key_type <= RS_KEY_F64 &&
+           (value_bits == 0 || value_bits == 32 || value_bits == 64);
+}
+
+// The 32-bit sorts (autotuned shapes, on-chip sorts of small arrays) serve
+// 32-bit keys with no or 32-bit values; everything else is a wide sort.
+bool kv_is_narrow(int key_type, int value_bits) {
+    return key_type <= RS_KEY_F32 && value_bits <= 32;
+}
+
+}  // namespace
+
+size_t rs_workspace_bytes_kv(size_t n, int key_type, int value_bits) {
+    if (n == 0 || !valid_kv_types(key_type, value_bits)) return 0;
+    if (kv_is_narrow(key_type, value_bits)) return layout_for(n, value_bits != 0).total;
+    return layout_wide(n, key_type >= RS_KEY_U64, (uint32_t)value_bits / 8).total;
+}
+
+rs_status rs_sort_kv_ex(void* d_keys, void* d_vals, size_t n, int key_type, int value_bits,
+                        void* cuda_stream, void* d_workspace, size_t workspace_bytes) {
+    if (!valid_kv_types(key_type, value_bits)) return RS_ERR_INVALID_ARG;
     if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
     if (n == 0) return RS_OK;
-    if (d_keys == nullptr || ((uintptr_t)d_keys & 7u) || ((uintptr_t)d_vals & 3u))
+    if (kv_is_narrow(key_type, value_bits)) {
+        if ((value_bits == 0) != (d_vals == nullptr)) return RS_ERR_INVALID_ARG;
+        return ex_sort(static_cast<uint32_t*>(d_keys), static_cast<uint32_t*>(d_vals), n,
+                       cuda_stream, d_workspace, workspace_bytes, key_type);
+    }
+    const size_t kb = key_type >= RS_KEY_U64 ? 8 : 4, vb = (size_t)value_bits / 8;
+    if (d_keys == nullptr || (vb == 0) != (d_vals == nullptr)) return RS_ERR_INVALID_ARG;
+    if (((uintptr_t)d_keys & (kb - 1)) || (vb && ((uintptr_t)d_vals & (vb - 1))))
         return RS_ERR_INVALID_ARG;
-    if (d_vals != nullptr) {
-        const uintptr_t k0 = (uintptr_t)d_keys, k1 = k0 + n * 8;
-        const uintptr_t v0 = (uintptr_t)d_vals, v1 = v0 + n * 4;
+    if (vb) {
+        const uintptr_t k0 = (uintptr_t)d_keys, k1 = k0 + n * kb;
+        const uintptr_t v0 = (uintptr_t)d_vals, v1 = v0 + n * vb;
         if (k0 < v1 && v0 < k1) return RS_ERR_INVALID_ARG;  // overlapping
     }
-    if (d_workspace == nullptr || workspace_bytes < layout_for64(n, d_vals != nullptr).total)
+    if (d_workspace == nullptr ||
+        workspace_bytes < layout_wide(n, kb == 8, (uint32_t)vb).total)
         return RS_ERR_INVALID_ARG;
-    return enqueue_sort64(reinterpret_cast<unsigned long long*>(d_keys), d_vals, (uint32_t)n,
-                          static_cast<cudaStream_t>(cuda_stream), d_workspace, workspace_bytes);
+    return enqueue_sort_wide(d_keys, d_vals, (uint32_t)n, (uint32_t)key_type, (uint32_t)vb,
+                             static_cast<cudaStream_t>(cuda_stream), d_workspace,
+                             workspace_bytes);
 }
 
 rs_status rs_stream_status(void* cuda_stream) {

@@ -62,10 +62,15 @@ static_assert(offsetof(Ctrl, hist) % 64 == 0, "histograms 64-byte aligned");
 //            positive-signed word gets its sign bit set, a negative-signed
 //            word is complemented (larger magnitude -> smaller word).
 // Both maps are bijections on 32-bit words, so sorting the mapped words
-// stably and mapping back is the stable sort in the typed order.
+// stably and mapping back is the stable sort in the typed order.  KEY_I64 and
+// KEY_F64 are the same maps on 64-bit words (bit 63 is the sign bit); KEY_U32
+// (and KEY_U64) is the identity on either width.
 constexpr uint32_t KEY_U32 = 0;
 constexpr uint32_t KEY_I32 = 1;
 constexpr uint32_t KEY_F32 = 2;
+constexpr uint32_t KEY_U64 = 3;
+constexpr uint32_t KEY_I64 = 4;
+constexpr uint32_t KEY_F64 = 5;
 
 __device__ __forceinline__ uint32_t key_to_ordered(uint32_t k, uint32_t type) {
     const uint32_t neg = type == KEY_F32 ? (uint32_t)((int32_t)k >> 31) : 0u;
@@ -74,6 +79,17 @@ __device__ __forceinline__ uint32_t key_to_ordered(uint32_t k, uint32_t type) {
 __device__ __forceinline__ uint32_t key_from_ordered(uint32_t k, uint32_t type) {
     const uint32_t neg = type == KEY_F32 ? ~(uint32_t)((int32_t)k >> 31) : 0u;
     return k ^ (neg | (type != KEY_U32 ? 0x80000000u : 0u));
+}
+__device__ __forceinline__ unsigned long long key_to_ordered(unsigned long long k, uint32_t type) {
+    const unsigned long long neg =
+        type == KEY_F64 ? (unsigned long long)((long long)k >> 63) : 0ull;
+    return k ^ (neg | (type == KEY_I64 || type == KEY_F64 ? 0x8000000000000000ull : 0ull));
+}
+__device__ __forceinline__ unsigned long long key_from_ordered(unsigned long long k,
+                                                               uint32_t type) {
+    const unsigned long long neg =
+        type == KEY_F64 ? ~(unsigned long long)((long long)k >> 63) : 0ull;
+    return k ^ (neg | (type == KEY_I64 || type == KEY_F64 ? 0x8000000000000000ull : 0ull));
 }
 
 // Status words of the decoupled look-back: a 2-bit flag above a count.

@@ -261,12 +261,13 @@ k_plan(Ctrl* __restrict__ ctrl, uint32_t n, uint32_t msd_allowed, uint32_t warp_
 // ---------------------------------------------------------------------------
 // k_hist8: the eight digit histograms of 64-bit keys (K = 64, D = 8) in one
 // read of the keys, added into hist[p * 256 + b] (zeroed by the caller), via
-// a CTA-private shared histogram.  Also clears the first pass's status array.
+// a CTA-private shared histogram.  Typed keys (TYPED) are counted by the
+// digits of their ordered words.  Also clears the first pass's status array.
 // ---------------------------------------------------------------------------
-template <int THREADS>
+template <int THREADS, bool TYPED>
 __global__ void __launch_bounds__(THREADS)
 k_hist8(const unsigned long long* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist,
-        uint4* __restrict__ clear, uint32_t clear_vec4) {
+        uint4* __restrict__ clear, uint32_t clear_vec4, uint32_t key_type) {
     __shared__ uint32_t s_h[PASSES64 * RADIX];
     const uint32_t tid = threadIdx.x;
     for (uint32_t i = tid; i < PASSES64 * RADIX; i += THREADS) s_h[i] = 0;
@@ -275,7 +276,8 @@ k_hist8(const unsigned long long* __restrict__ keys, uint32_t n, uint32_t* __res
     for (uint32_t i = gtid; i < clear_vec4; i += gsize) clear[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     for (uint32_t i = gtid; i < n; i += gsize) {
-        const unsigned long long k = __ldcs(keys + i);
+        unsigned long long k = __ldcs(keys + i);
+        if (TYPED) k = key_to_ordered(k, key_type);
         const uint32_t lo = (uint32_t)k, hi = (uint32_t)(k >> 32);
 #pragma unroll
         for (uint32_t p = 0; p < 4; ++p) {

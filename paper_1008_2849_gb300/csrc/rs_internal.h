@@ -115,14 +115,32 @@ Layout layout_for(size_t n, bool pairs);
 rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
                        void* workspace, size_t workspace_bytes, uint32_t key_type = 0);
 
-// 64-bit keys (eight passes), optionally carrying 32-bit values.
-Layout layout_for64(size_t n, bool pairs);
-rs_status enqueue_sort64(unsigned long long* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
-                         void* workspace, size_t workspace_bytes);
+// Wide items: 64-bit keys (eight passes; key_type KEY_U64, KEY_I64 or
+// KEY_F64) carrying no, 32-bit or 64-bit values (val_bytes 0, 4 or 8), and
+// 32-bit keys (KEY_U32, KEY_I32, KEY_F32) carrying 64-bit values.  Every
+// array size takes the scatter passes.
+Layout layout_wide(size_t n, bool key64, uint32_t val_bytes);
+rs_status enqueue_sort_wide(void* keys, void* vals, uint32_t n, uint32_t key_type,
+                            uint32_t val_bytes, cudaStream_t stream, void* workspace,
+                            size_t workspace_bytes);
+// Scatter-pass tiles of the wide sorts: 384 threads, items per thread.
+constexpr int kWideThreads = 384;
+constexpr int kWideItems64 = 7;     // 64-bit keys, no or 32-bit values
+constexpr int kWideItems64V64 = 6;  // 64-bit keys, 64-bit values
+constexpr int kWideItems32V64 = 7;  // 32-bit keys, 64-bit values
+// One scatter pass of 64-bit keys (rs_sort64.cu); wide = 64-bit status words.
+rs_status launch_pass_k64(uint32_t key_type, uint32_t val_bytes, bool wide,
+                          unsigned long long* ka, void* va, unsigned long long* kb, void* vb,
+                          uint32_t n, uint32_t pass, Ctrl* ctrl, uint32_t* sticky, void* status,
+                          void* status_clear, cudaStream_t stream);
 
 // Enqueue the digit histograms of n keys into hist[4 * 256] (zeroed first).
 rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
                              cudaStream_t stream);
+// The same, added into hist (zeroed by the caller), counting the digits of
+// the ordered words of typed keys, and clearing clear_bytes at `clear`.
+rs_status enqueue_hist4(const uint32_t* keys, uint32_t n, uint32_t* hist, void* clear,
+                        size_t clear_bytes, uint32_t key_type, cudaStream_t stream);
 
 // Segmented scatter passes: per-tile geometry and per-segment bucket bases
 // built on the device, and an upper bound of the tile count for the launch.

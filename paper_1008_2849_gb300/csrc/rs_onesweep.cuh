@@ -13,12 +13,13 @@
 namespace rs {
 
 // ---------------------------------------------------------------------------
-// Shared-memory plan of k_onesweep (offsets in 32-bit words; KW = words per
-// key, 1 for 32-bit keys and 2 for 64-bit keys):
-//   in_k[2][TILE + pad]  input keys of the current and the next tile; the
+// Shared-memory plan of k_onesweep (offsets in 32-bit words; KW and VW =
+// words per key and per value, 1 for 32-bit and 2 for 64-bit items):
+//   in_k[2][TILE * max(KW, VW) + pad]
+//                        input keys of the current and the next tile; the
 //                        current tile's values are staged here once its keys
 //                        are ranked
-//   in_v[TILE + pad]     input values of the current tile (key-value sorts)
+//   in_v[TILE * VW + pad] input values of the current tile (key-value sorts)
 // An input buffer holds its tile at the same offset modulo 16 bytes as in
 // global memory (a skew of up to 12 bytes, hence the 16-byte pad), so that
 // the tile's 16-byte-aligned middle always arrives by one bulk copy.
@@ -27,17 +28,18 @@ namespace rs {
 //                        tile positions while the tile is ranked
 //   mask[WARPS][RADIX]   per-warp peer masks of the ranking (zero between uses)
 // ---------------------------------------------------------------------------
-template <int THREADS, int ITEMS, bool PAIRS, int KW = 1>
+template <int THREADS, int ITEMS, bool PAIRS, int KW = 1, int VW = 1>
 struct OnesweepSmem {
     static constexpr uint32_t WARPS = THREADS / 32;
     static constexpr uint32_t TILE = THREADS * ITEMS;
     static constexpr uint32_t PAD = 4;                   // words after every input buffer
-    static constexpr uint32_t KBUF = TILE * KW + PAD;    // words per key buffer
+    static constexpr uint32_t BW = PAIRS && VW > KW ? VW : KW;  // words per buffer item
+    static constexpr uint32_t KBUF = TILE * BW + PAD;    // words per key buffer
     static constexpr uint32_t IN_K = 0;
     static constexpr uint32_t IN_V = IN_K + 2 * KBUF;
-    static constexpr uint32_t STG = IN_V + (PAIRS ? TILE + PAD : 0);
+    static constexpr uint32_t STG = IN_V + (PAIRS ? TILE * VW + PAD : 0);
     static constexpr uint32_t WCNT = STG + TILE * KW;
-    static_assert(KBUF % 4 == 0 && (TILE + PAD) % 4 == 0 && STG % KW == 0,
+    static_assert(KBUF % 4 == 0 && (TILE * VW + PAD) % 4 == 0 && STG % KW == 0,
                   "input buffers 16-byte aligned for the bulk copies, stage aligned to keys");
     static constexpr uint32_t MASK = WCNT + WARPS * RADIX;
     static constexpr uint32_t WORDS = MASK + WARPS * RADIX;
@@ -59,7 +61,7 @@ struct OnesweepSmem {
 // three items before and after it arrive by per-thread asynchronous copies on
 // the same barrier.  As soon as tile i+1's keys have landed its per-warp digit
 // counts are taken and its tile counts published.  Keys are 32-bit (K =
-// uint32_t) or 64-bit (K = unsigned long long, eight passes); values 32-bit.
+// uint32_t) or 64-bit (K = unsigned long long, eight passes); values (V) too.
 //
 // Item order: warp w owns tile items [w*32*ITEMS, (w+1)*32*ITEMS); its item j
 // on lane l is tile item w*32*ITEMS + j*32 + l, so the (warp, j, lane) order
@@ -97,28 +99,31 @@ struct OnesweepSmem {
 //     256 prepare the next tile (its counts, AGG and warp bases).  Every
 //     global store is checked against n (ERR_BOUNDS instead of a fault).
 // ---------------------------------------------------------------------------
-// Typed keys (TYPED): the first pass that moves data maps every key it reads
-// onto its ordered unsigned word (key_to_ordered), so all digits, ranks and
-// staged keys of the sort are those of the ordered words, and the last pass
-// maps every key it stores back (key_from_ordered).  Values are untouched.
+// Typed keys (TYPED; 32-bit or 64-bit): the first pass that moves data maps
+// every key it reads onto its ordered unsigned word (key_to_ordered), so all
+// digits, ranks and staged keys of the sort are those of the ordered words,
+// and the last pass maps every key it stores back (key_from_ordered).  Values
+// are untouched.
 //
 // Segmented sorts (SEG): tiles never straddle a segment.  tile_geo[t] =
 // (first item, item count, first tile of its segment, segment) for every tile
 // of the large segments; seg_gofs[s][pass][b] is the absolute first output
 // slot of bucket b of segment s; the number of tiles is ctrl->seg_tiles.
 template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WINDOW, bool SEG,
-          bool TYPED, typename K = uint32_t>
+          bool TYPED, typename K = uint32_t, typename V = uint32_t>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS)
-k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
-           K* __restrict__ kb, uint32_t* __restrict__ vb,
+k_onesweep(K* __restrict__ ka, V* __restrict__ va,
+           K* __restrict__ kb, V* __restrict__ vb,
            uint32_t n, uint32_t pass, uint32_t slot, uint32_t num_tiles, Ctrl* __restrict__ ctrl,
            uint32_t* __restrict__ sticky, S* __restrict__ status, S* __restrict__ status_clear,
            uint32_t clear_words, uint32_t spin_limit, uint32_t debug,
            const uint4* __restrict__ tile_geo, const uint32_t* __restrict__ seg_gofs,
            uint32_t key_type) {
-    using L = OnesweepSmem<THREADS, ITEMS, PAIRS, (int)(sizeof(K) / 4)>;
+    using L = OnesweepSmem<THREADS, ITEMS, PAIRS, (int)(sizeof(K) / 4), (int)(sizeof(V) / 4)>;
     using SW = StatusWord<S>;
-    static_assert(sizeof(K) == 4 || !TYPED, "typed keys are 32-bit");
+    static_assert(sizeof(K) == 4 || sizeof(K) == 8, "32-bit or 64-bit keys");
+    static_assert(sizeof(V) == 4 || sizeof(V) == 8, "32-bit or 64-bit values");
+    constexpr uint32_t NPASS = sizeof(K) == 8 ? PASSES64 : PASSES;
     static_assert(THREADS >= (int)RADIX && THREADS % 32 == 0, "one thread per digit");
     static_assert(RADIX_BITS == 8, "digits are whole bytes of the key");
     constexpr uint32_t WARPS = L::WARPS;
@@ -143,7 +148,7 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
     // Key buffer b (as K*), not yet skewed.
     auto key_buf = [&](uint32_t b) { return reinterpret_cast<K*>(smem + L::IN_K + b * L::KBUF); };
     uint32_t* const s_wcnt = smem + L::WCNT;
-    const uint32_t* const s_in_v = smem + L::IN_V;
+    const V* const s_in_v = reinterpret_cast<const V*>(smem + L::IN_V);
     __shared__ uint32_t s_gbase[RADIX];  // G[pass][b]
     __shared__ uint32_t s_gofs[RADIX];   // G + before_tile - tile_excl, per tile
     __shared__ uint32_t s_cnt[RADIX];    // digit counts of the next tile to rank
@@ -174,7 +179,7 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
     uint32_t map_in = KEY_U32, map_out = KEY_U32;
     if (TYPED) {
         bool first = true, last = true;
-        for (uint32_t q = 0; q < PASSES; ++q) {
+        for (uint32_t q = 0; q < NPASS; ++q) {
             if (ctrl->dir[q] == DIR_SKIP) continue;
             if (q < pass) first = false;
             if (q > pass) last = false;
@@ -188,8 +193,8 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
     };
     const K* __restrict__ src_k = dir == DIR_A_TO_B ? ka : kb;
     K* __restrict__ dst_k = dir == DIR_A_TO_B ? kb : ka;
-    const uint32_t* __restrict__ src_v = dir == DIR_A_TO_B ? va : vb;
-    uint32_t* __restrict__ dst_v = dir == DIR_A_TO_B ? vb : va;
+    const V* __restrict__ src_v = dir == DIR_A_TO_B ? va : vb;
+    V* __restrict__ dst_v = dir == DIR_A_TO_B ? vb : va;
 
     for (uint32_t i = tid; i < 2 * WARPS * RADIX / 4; i += THREADS)
         reinterpret_cast<uint4*>(s_wcnt)[i] = make_uint4(0, 0, 0, 0);  // wcnt and mask
@@ -220,7 +225,7 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
     // Start copying the g.y items from src + g.x into buffer dst at the
     // tile's skew (collective): the 16-byte-aligned middle by one bulk copy,
     // the few items before and after it by per-thread copies, all completing
-    // on `bar`.  Items are keys (K) or values (32-bit).
+    // on `bar`.  Items are keys (K) or values (V).
     auto issue_copy = [&](auto* dst, const auto* src, uint4 g, uint64_t* bar) {
         using T = std::remove_cv_t<std::remove_pointer_t<decltype(src)>>;
         constexpr uint32_t PER16 = 16 / sizeof(T);  // items per 16 bytes
@@ -343,7 +348,7 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
     // once they are published.
     if (s_ids[0] >= num_tiles) return;
     issue_copy(key_buf(0), src_k, s_geo[0], &s_bar[0]);
-    if (PAIRS) issue_copy(smem + L::IN_V, src_v, s_geo[0], &s_bar[2]);
+    if (PAIRS) issue_copy(reinterpret_cast<V*>(smem + L::IN_V), src_v, s_geo[0], &s_bar[2]);
     wait_bar(0);
     count_slots_of(0, s_geo[0], warp);
     __syncthreads();
@@ -376,8 +381,10 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
         const uint32_t valid = geo.y;
         const uint32_t first_tile = geo.z;  // look-back stops here
         K* const in_k = key_buf(buf) + skew_of(src_k, geo);
-        const uint32_t* const in_v = s_in_v + (PAIRS ? skew_of(src_v, geo) : 0u);
-        uint32_t* const in_kv = reinterpret_cast<uint32_t*>(in_k);  // staged values
+        const V* const in_v = s_in_v + (PAIRS ? skew_of(src_v, geo) : 0u);
+        // Staged values: the whole key buffer is free once the keys are
+        // ranked; its unskewed start is 16-byte aligned.
+        V* const in_kv = reinterpret_cast<V*>(key_buf(buf));
 
         // ---- 2. rank, and stage the keys ------------------------------------
         uint32_t* const cnt = s_wcnt + warp * RADIX;
@@ -510,7 +517,7 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
         // Every thread stages its own items' values (the key buffer is free).
         if (PAIRS) {
             wait_bar(2);
-            uint32_t vv[ITEMS];
+            V vv[ITEMS];
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) vv[j] = in_v[wofs + j * 32 + lane];
             if (valid == TILE) {
@@ -524,7 +531,8 @@ k_onesweep(K* __restrict__ ka, uint32_t* __restrict__ va,
         }
         __syncthreads();
         if (s_flag) break;  // an error somewhere: write nothing more (no copy is in flight)
-        if (PAIRS && have_next) issue_copy(smem + L::IN_V, src_v, ngeo, &s_bar[2]);
+        if (PAIRS && have_next)
+            issue_copy(reinterpret_cast<V*>(smem + L::IN_V), src_v, ngeo, &s_bar[2]);
 
         // ---- 4. the next tile's counts, prefix and bases || this tile's stores
         if (have_next && tid < RADIX) prep_tile(nxt, ngeo.z);

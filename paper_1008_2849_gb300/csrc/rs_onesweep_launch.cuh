@@ -17,15 +17,15 @@ RS_TILE_SHAPES(RS_SHAPE_STRUCT)
 #undef RS_SHAPE_STRUCT
 
 template <int THREADS, int ITEMS, int MIN_BLOCKS, int WINDOW, bool PAIRS, typename S, bool SEG,
-          bool TYPED, typename K = uint32_t>
-static rs_status launch_onesweep_shape(K* ka, uint32_t* va, K* kb, uint32_t* vb,
+          bool TYPED, typename K = uint32_t, typename V = uint32_t>
+static rs_status launch_onesweep_shape(K* ka, V* va, K* kb, V* vb,
                                        uint32_t n, uint32_t pass, uint32_t slot, Ctrl* ctrl,
                                        uint32_t* sticky,
                                        void* status, void* status_clear, const SegView& seg,
                                        uint32_t key_type, cudaStream_t stream) {
-    using L = OnesweepSmem<THREADS, ITEMS, PAIRS, (int)(sizeof(K) / 4)>;
+    using L = OnesweepSmem<THREADS, ITEMS, PAIRS, (int)(sizeof(K) / 4), (int)(sizeof(V) / 4)>;
     constexpr uint32_t TILE = L::TILE;
-    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW, SEG, TYPED, K>;
+    auto kern = k_onesweep<THREADS, ITEMS, MIN_BLOCKS, PAIRS, S, WINDOW, SEG, TYPED, K, V>;
     static std::atomic<int> ctas_per_sm[64];  // per device: resident CTAs per SM (0: unknown)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RS_ERR_CUDA;

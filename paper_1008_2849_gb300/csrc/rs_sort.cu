@@ -47,8 +47,8 @@ Layout layout_for(size_t n, bool pairs) {
     return L;
 }
 
-static rs_status launch_hist(const uint32_t* keys, uint32_t n, uint32_t* hist, void* clear,
-                             size_t clear_bytes, uint32_t key_type, cudaStream_t stream) {
+rs_status enqueue_hist4(const uint32_t* keys, uint32_t n, uint32_t* hist, void* clear,
+                        size_t clear_bytes, uint32_t key_type, cudaStream_t stream) {
     DeviceInfo di;
     rs_status st = device_info(&di);
     if (st != RS_OK) return st;
@@ -98,7 +98,7 @@ rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
                              cudaStream_t stream) {
     if (cudaMemsetAsync(hist, 0, PASSES * RADIX * sizeof(uint32_t), stream) != cudaSuccess)
         return RS_ERR_CUDA;
-    return launch_hist(keys, n, hist, nullptr, 0, KEY_U32, stream);
+    return enqueue_hist4(keys, n, hist, nullptr, 0, KEY_U32, stream);
 }
 
 rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
@@ -135,7 +135,7 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
         (uint32_t)ck.warp_max < warp_sort_capacity() ? (uint32_t)ck.warp_max : warp_sort_capacity();
 
     if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return RS_ERR_CUDA;
-    st = launch_hist(keys, n, &ctrl->hist[0][0], status[0], status_bytes, key_type, stream);
+    st = enqueue_hist4(keys, n, &ctrl->hist[0][0], status[0], status_bytes, key_type, stream);
     if (st != RS_OK) return st;
     note_launch_begin(KK_PLAN, stream);
     k_plan<PASSES><<<1, 1024, 0, stream>>>(ctrl, n, msd ? 1u : 0u, warp_max, small_sort_capacity(),

@@ -47,6 +47,8 @@ SIGNATURES = {
     "rs_workspace_bytes": (_sz, [_sz, _int, _u32]),
     "rs_sort64_ex": (_int, [_vp, _vp, _sz, _vp, _vp, _sz]),
     "rs_workspace_bytes64": (_sz, [_sz, _int]),
+    "rs_sort_kv_ex": (_int, [_vp, _vp, _sz, _int, _int, _vp, _vp, _sz]),
+    "rs_workspace_bytes_kv": (_sz, [_sz, _int, _int]),
     "rs_stream_status": (_int, [_vp]),
     "rs_status_string": (ctypes.c_char_p, [_int]),
     "rs_digit_histograms_ex": (_int, [_vp, _sz, _vp, _vp]),
@@ -217,6 +219,43 @@ def sort64_ex(keys, vals, workspace, stream=None) -> None:
                               None if vals is None else _dev_ptr(vals, "vals"), keys.numel(),
                               _stream_handle(stream), workspace.data_ptr(), workspace.numel()),
            "rs_sort64_ex")
+
+
+# Key types of rs_sort_kv_ex (rs_key_type) and their word widths in bytes.
+KV_KEY_TYPES = {"u32": (0, 4), "i32": (1, 4), "f32": (2, 4),
+                "u64": (3, 8), "i64": (4, 8), "f64": (5, 8)}
+
+
+def workspace_bytes_kv(n: int, key_type: str, value_bits: int) -> int:
+    return int(lib().rs_workspace_bytes_kv(int(n), KV_KEY_TYPES[key_type][0], int(value_bits)))
+
+
+def sort_kv_ex(keys, vals, key_type: str, workspace, stream=None) -> None:
+    """Enqueue an in-place stable sort of keys read as ``key_type`` (int32
+    tensors for the 32-bit types, int64 for the 64-bit ones, holding the bit
+    patterns), carrying int32 or int64 values, or None."""
+    code, kw = KV_KEY_TYPES[key_type]
+    value_bits = 0
+    vp = None
+    if vals is not None:
+        if vals.numel() != keys.numel():
+            raise ValueError("keys and vals differ in length")
+        value_bits = 8 * vals.element_size()
+        vp = _dev_ptr(vals, "vals", vals.element_size())
+    _check(lib().rs_sort_kv_ex(_dev_ptr(keys, "keys", kw), vp, keys.numel(), code, value_bits,
+                               _stream_handle(stream), workspace.data_ptr(), workspace.numel()),
+           "rs_sort_kv_ex")
+
+
+def sort_kv(keys, vals=None, key_type: str = "u64", stream=None) -> None:
+    """Synchronous ``sort_kv_ex`` with a workspace allocated for the call."""
+    import torch
+    value_bits = 0 if vals is None else 8 * vals.element_size()
+    nbytes = max(workspace_bytes_kv(keys.numel(), key_type, value_bits), 1)
+    raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=keys.device)
+    pad = (-raw.data_ptr()) % 256
+    sort_kv_ex(keys, vals, key_type, raw[pad:pad + nbytes], stream)
+    check_stream(stream)
 
 
 def sort64(keys, vals=None, stream=None) -> None:

@@ -327,6 +327,136 @@ def pin_sort64_bruteforce(lib=None):
 
 KEY64_PINS = (pin_sort64_numpy, pin_sort64_bruteforce)
 
+
+# ---------------------------------------------------------------------------
+# Items of every width (Sec. 1: larger items sort like the 32-bit ones): keys
+# u32, i32, f32, u64, i64, f64 with no, 32-bit or 64-bit values.  Pinned
+# against numpy's stable argsort of the typed view, the standard's listing of
+# the binary64 totalOrder, the brute-force stable rank, and the radix-sort
+# oracles above (an independent algorithm with the same unique answer).
+# ---------------------------------------------------------------------------
+def _golden_double_order():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "double_total_order.txt")
+    words = []
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            words.append(int(line.split()[0], 16))
+    return np.array(words, dtype=np.uint64)
+
+
+def _values64(n):
+    """Index-derived 64-bit payloads whose halves differ: a value carried
+    only in part, or from the wrong item, shows."""
+    i = np.arange(n, dtype=np.uint64)
+    return (i ^ np.uint64(0xA5A5A5A5)) << np.uint64(32) | i
+
+
+def _kv_keys(key_type, n, seed):
+    """Keys of every reading: random words with duplicates and extremes;
+    float keys without NaNs and zeros (numpy orders those apart from
+    totalOrder; the golden listings cover them)."""
+    if key_type.endswith("32"):
+        k = inputs.keys("uniform", n, seed)
+        k[::6] = k[1::6][: k[::6].size]
+        if key_type == "f32":
+            exp = (k >> np.uint32(24)) % np.uint32(255)
+            k = (k & np.uint32(0x807FFFFF)) | (exp << np.uint32(23))
+            k[(k & np.uint32(0x7FFFFFFF)) == 0] = 0x3F800000
+        return k
+    k = _keys64(n, seed)
+    k[::6] = k[1::6][: k[::6].size]
+    k[:4] = np.array([0, 0x7FFFFFFFFFFFFFFF, 0x8000000000000000, 0xFFFFFFFFFFFFFFFF],
+                     dtype=np.uint64)
+    if key_type == "f64":
+        exp = (k >> np.uint64(52)) % np.uint64(2047)         # never the NaN exponent 2047
+        k = (k & np.uint64(0x800FFFFFFFFFFFFF)) | (exp << np.uint64(52))
+        k[(k & np.uint64(0x7FFFFFFFFFFFFFFF)) == 0] = 0x3FF0000000000000
+    return k
+
+
+_NUMPY_VIEW = {"u32": np.uint32, "i32": np.int32, "f32": np.float32,
+               "u64": np.uint64, "i64": np.int64, "f64": np.float64}
+
+
+def pin_kv_numpy(lib=None):
+    """Every key type with no, 32-bit and 64-bit values: numpy's stable
+    argsort of the typed view."""
+    n = 3000
+    for i, kt in enumerate(_NUMPY_VIEW):
+        k = _kv_keys(kt, n, seed=60 + i)
+        order = np.argsort(k.view(_NUMPY_VIEW[kt]), kind="stable")
+        for v in (None, inputs.index_values(n), _values64(n)):
+            ko, vo = oracle.sort_kv(k, v, kt, lib=lib)
+            assert np.array_equal(ko, k[order])
+            if v is not None:
+                assert np.array_equal(vo, v[order])
+
+
+def pin_kv_double_total_order(lib=None):
+    """The listed binary64 totalOrder sequence, shuffled, comes back in that
+    order.  The listing itself is checked against numpy's float64 reading of
+    its non-NaN words (ascending, -0 and +0 equal)."""
+    want = _golden_double_order()
+    f = want.view(np.float64)
+    finite = ~np.isnan(f)
+    assert np.all(np.diff(f[finite]) >= 0)
+    assert np.count_nonzero(np.diff(f[finite]) == 0) == 1        # only -0, +0
+    for seed in (61, 62, 63):
+        perm = np.argsort(inputs.uniform01(seed, want.size, 0), kind="stable")
+        ko, vo = oracle.sort_kv(want[perm], _values64(want.size), "f64", lib=lib)
+        assert np.array_equal(ko, want)
+        assert np.array_equal(vo, _values64(want.size)[np.argsort(perm)])
+
+
+def pin_kv_bruteforce(lib=None):
+    """The closed-form stable rank on tiny arrays over small alphabets of
+    each reading (signed values straddling zero, floats of both signs)."""
+    alphabets = {
+        "i64": [0xFFFFFFFFFFFFFFFF, 0, 1, 0x8000000000000000, 0x7FFFFFFFFFFFFFFF],
+        "u64": [0xFFFFFFFFFFFFFFFF, 0, 1, 0x8000000000000000, 0x7FFFFFFFFFFFFFFF],
+        "f64": [0xBFF0000000000000, 0x3FF0000000000000, 0xC000000000000000,
+                0x0000000000000001, 0x8000000000000001],
+        "i32": [0xFFFFFFFF, 0, 1, 0x80000000, 0x7FFFFFFF],
+    }
+    for kt, alpha in alphabets.items():
+        dt = np.uint64 if kt.endswith("64") else np.uint32
+        for seed in range(4):
+            pick = inputs.splitmix32(70 + seed, 9, 0) % np.uint32(len(alpha))
+            k = np.array([alpha[i] for i in pick], dtype=dt)
+            vals = k.view(_NUMPY_VIEW[kt]).tolist()
+            rank = stable_rank_bruteforce(vals)
+            v = _values64(k.size)
+            ko, vo = oracle.sort_kv(k, v, kt, lib=lib)
+            want_v = np.empty_like(v)
+            want_v[rank] = v
+            assert np.array_equal(vo, want_v)
+            want_k = np.empty_like(k)
+            want_k[rank] = k
+            assert np.array_equal(ko, want_k)
+
+
+def pin_kv_radix_oracles(lib=None):
+    """Unsigned keys: the merge sort agrees with the LSD radix-sort oracles
+    (32-bit keys, 64-bit keys with 32-bit values) and carries 64-bit values
+    along the same permutation as 32-bit ones."""
+    n = 5000
+    k32 = _kv_keys("u32", n, seed=80)
+    k64 = _kv_keys("u64", n, seed=81)
+    v32 = inputs.index_values(n)
+    ko, vo = oracle.sort_kv(k32, v32, "u32", lib=lib)
+    rk, rv = oracle.sort_pairs(k32, v32)
+    assert np.array_equal(ko, rk) and np.array_equal(vo, rv)
+    ko, vo = oracle.sort_kv(k64, v32, "u64", lib=lib)
+    rk, rv = oracle.sort_pairs64(k64, v32)
+    assert np.array_equal(ko, rk) and np.array_equal(vo, rv)
+    _, wide = oracle.sort_kv(k64, _values64(n), "u64", lib=lib)
+    assert np.array_equal(wide, _values64(n)[rv])
+
+
+KV_PINS = (pin_kv_numpy, pin_kv_double_total_order, pin_kv_bruteforce, pin_kv_radix_oracles)
+
 TYPED_PINS = (pin_typed_i32_numpy, pin_typed_f32_numpy, pin_typed_f32_total_order,
               pin_typed_stability, pin_typed_segmented)
 

@@ -83,3 +83,38 @@ def test_host_side_argument_errors(lib):
     assert lib.rs_sort_pairs_ex(ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), 100, None, None, 0) == 1
     assert lib.rs_digit_histograms_ex(ctypes.c_void_p(4096), 10, None, None) == 1
     assert lib.rs_sort_pairs_host(None, None, None, None, 10) == 1
+
+
+def test_workspace_bytes_kv(lib):
+    from paper_1008_2849_gb300 import rs
+    n = 1 << 20
+    # 32-bit keys with no or 32-bit values: the workspace of the 32-bit sorts.
+    assert rs.workspace_bytes_kv(n, "u32", 0) == rs.workspace_bytes(n, False)
+    assert rs.workspace_bytes_kv(n, "f32", 32) == rs.workspace_bytes(n, True)
+    assert rs.workspace_bytes_kv(n, "u64", 32) == rs.workspace_bytes64(n, True)
+    assert rs.workspace_bytes_kv(n, "i64", 0) == rs.workspace_bytes64(n, False)
+    # Wide items: alternate key and value buffers plus two status arrays of
+    # 1 KiB per tile (2304 items at least) and the control block.
+    for kt, kb in (("u32", 4), ("u64", 8), ("f64", 8)):
+        ws = rs.workspace_bytes_kv(n, kt, 64)
+        assert (kb + 8) * n <= ws <= (kb + 8) * n + 2 * (n // 2304 + 1) * 1024 + 65536
+        assert ws % 256 == 0
+    assert rs.workspace_bytes_kv(0, "u64", 64) == 0
+    assert lib.rs_workspace_bytes_kv(100, 6, 0) == 0      # unknown key type
+    assert lib.rs_workspace_bytes_kv(100, 3, 16) == 0     # unknown value width
+
+
+def test_kv_host_side_argument_errors(lib):
+    k, v, ws = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 30), ctypes.c_void_p(1 << 34)
+    big = 1 << 40
+    assert lib.rs_sort_kv_ex(k, v, 100, 6, 64, None, ws, big) == 1           # key type
+    assert lib.rs_sort_kv_ex(k, v, 100, 3, 16, None, ws, big) == 1           # value width
+    assert lib.rs_sort_kv_ex(k, None, 100, 3, 64, None, ws, big) == 1        # values missing
+    assert lib.rs_sort_kv_ex(k, v, 100, 3, 0, None, ws, big) == 1            # values unexpected
+    assert lib.rs_sort_kv_ex(ctypes.c_void_p((1 << 20) + 4), v, 100, 3, 64, None, ws, big) == 1
+    assert lib.rs_sort_kv_ex(k, ctypes.c_void_p((1 << 30) + 4), 100, 0, 64, None, ws, big) == 1
+    assert lib.rs_sort_kv_ex(k, ctypes.c_void_p((1 << 20) + 512), 100, 3, 64, None, ws, big) == 1
+    assert lib.rs_sort_kv_ex(k, v, 100, 4, 64, None, None, 0) == 1           # no workspace
+    assert lib.rs_sort_kv_ex(k, v, 100, 4, 64, None, ws, 64) == 1            # too small
+    assert lib.rs_sort_kv_ex(k, v, 1 << 32, 4, 64, None, ws, big) == 5       # n >= 2^32
+    assert lib.rs_sort_kv_ex(None, None, 0, 5, 0, None, None, 0) == 0        # n = 0

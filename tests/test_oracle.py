@@ -155,3 +155,42 @@ def test_key64_pins_reject_mutant(name, tmp_path):
         except AssertionError:
             failures.append(pin.__name__)
     assert failures, "no pin rejects mutant %s" % name
+
+
+@pytest.mark.parametrize("pin", oracle_pins.KV_PINS, ids=lambda f: f.__name__)
+def test_kv_oracle_pin(pin):
+    pin()
+
+
+KV_MUTANTS = {
+    "i64_compared_unsigned": ("    if (key_type == 4) return (int64_t)x < (int64_t)y;",
+                              "    if (key_type == 4) return x < y;"),
+    "f64_negatives_not_reversed": ("    return mx > my;                /* both negative */",
+                                   "    return mx < my;                /* both negative */"),
+    "value_half_carried": ("(const unsigned char*)vals_in + vb * idx[i],\n                   vb);",
+                           "(const unsigned char*)vals_in + vb * idx[i],\n                   4);"),
+    "unstable_merge": ("        if (kv_less(keys, idx[j], idx[i], key_type))",
+                       "        if (!kv_less(keys, idx[i], idx[j], key_type))"),
+    "f64_read_as_i64": ("    if (key_type == 3) return x < y;\n    if (key_type == 4)",
+                        "    if (key_type == 3) return x < y;\n    if (key_type >= 4)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(KV_MUTANTS))
+def test_kv_pins_reject_mutant(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "rs_oracle.c")).read()
+    old, new = KV_MUTANTS[name]
+    assert src.count(old) == 1, "mutation anchor not found: %s" % name
+    mutated = tmp_path / ("%s.c" % name)
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / ("lib%s.so" % name)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                           "-o", str(so), str(mutated)])
+    lib = oracle._bind(str(so))
+    failures = []
+    for pin in oracle_pins.KV_PINS:
+        try:
+            pin(lib)
+        except AssertionError:
+            failures.append(pin.__name__)
+    assert failures, "no pin rejects mutant %s" % name
