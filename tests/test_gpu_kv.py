@@ -160,5 +160,5 @@ def test_kv_argument_errors(rs):
                            0, 64, None, w, ws.numel()) == 1        # misaligned 64-bit values
     assert L.rs_sort_kv_ex(ctypes.c_void_p(k.data_ptr()), ctypes.c_void_p(v.data_ptr()), 16,
                            4, 64, None, w, 16) == 1                # workspace too small
-    assert L.rs_sort_kv_ex(ctypes.c_void_p(k.data_ptr()), ctypes.c_void_p(k.data_ptr() + 64), 8,
+    assert L.rs_sort_kv_ex(ctypes.c_void_p(k.data_ptr()), ctypes.c_void_p(k.data_ptr() + 32), 8,
                            5, 64, None, w, ws.numel()) == 1        # overlapping
