@@ -26,7 +26,7 @@ from __future__ import annotations
 import collections
 import dataclasses
 import time
-from typing import List, Optional
+from typing import Callable, List, Optional
 
 import numpy as np
 
@@ -159,13 +159,18 @@ class GpuExecutor:
 
 class SortServer:
     def __init__(self, executor, budget_bytes: int = 60 * 10**9, max_inflight: int = 8,
-                 small_max: int = 1 << 16, batch_items: int = 1 << 22, keep_results=False):
+                 small_max: int = 1 << 16, batch_items: int = 1 << 22, keep_results=False,
+                 on_done: Optional[Callable[[Done], None]] = None):
+        """on_done, if given, receives every completed request as it is taken
+        (with its result views when keep_results); the returned list then
+        holds the requests and latencies only, so results are not retained."""
         self.ex = executor
         self.budget = int(budget_bytes)
         self.max_inflight = max_inflight
         self.small_max = small_max
         self.batch_items = batch_items
         self.keep = keep_results
+        self.on_done = on_done
         self.peak_bytes = 0
 
     def run(self, requests: List[Request], realtime: bool = True) -> dict:
@@ -194,7 +199,11 @@ class SortServer:
                 if self.ex.poll(h):
                     tdone = now()
                     for r, (k, v) in zip(rs_, self.ex.take(h, self.keep)):
-                        done.append(Done(r, tdone - r.arrival if realtime else tdone, len(rs_), k, v))
+                        d = Done(r, tdone - r.arrival if realtime else tdone, len(rs_), k, v)
+                        if self.on_done is not None:
+                            self.on_done(d)
+                            d = Done(d.request, d.latency, d.batch)
+                        done.append(d)
                     used -= b
                 else:
                     still.append((h, rs_, b))

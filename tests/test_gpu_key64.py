@@ -134,6 +134,8 @@ def test_key64_wide_status_2pow30_plus(rs):
     del idx
     rs.sort64(keys, vals)
     assert bool((keys[1:] >= keys[:-1]).all())
+    # Range first: indexing by an out-of-range value would be a device-side error.
+    assert bool(((vals >= 0) & (vals.long() < n)).all())
     assert bool((orig[vals.long()] == keys).all())
     same = keys[1:] == keys[:-1]
     assert bool((vals[1:][same] > vals[:-1][same]).all())

@@ -215,6 +215,8 @@ def test_wide_status_2pow30_plus(rs):
     rs.sort_pairs(keys, vals)
     ku = keys.to(torch.int64) & 0xFFFFFFFF
     assert bool((ku[1:] >= ku[:-1]).all())
+    # Range first: indexing by an out-of-range value would be a device-side error.
+    assert bool(((vals >= 0) & (vals.long() < n)).all())
     assert bool((orig[vals.long()] == keys).all())
     same = ku[1:] == ku[:-1]
     assert bool((vals[1:][same] > vals[:-1][same]).all())
