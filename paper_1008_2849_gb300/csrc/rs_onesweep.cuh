@@ -20,6 +20,9 @@ namespace rs {
 //                        current tile's values are staged here once its keys
 //                        are ranked
 //   in_v[TILE * VW + pad] input values of the current tile (key-value sorts)
+// 32-bit keys with 32-bit values (PACKED) keep one key buffer instead, and
+// their stage holds (key, value) slots of 8 bytes written while ranking; the
+// next tile's keys and values are copied in once the current tile is ranked.
 // An input buffer holds its tile at the same offset modulo 16 bytes as in
 // global memory (a skew of up to 12 bytes, hence the 16-byte pad), so that
 // the tile's 16-byte-aligned middle always arrives by one bulk copy.
@@ -33,14 +36,18 @@ struct OnesweepSmem {
     static constexpr uint32_t WARPS = THREADS / 32;
     static constexpr uint32_t TILE = THREADS * ITEMS;
     static constexpr uint32_t PAD = 4;                   // words after every input buffer
+    // 32-bit keys with 32-bit values: one key buffer, and every staged slot
+    // holds its key and value together (8 bytes).
+    static constexpr bool PACKED = PAIRS && KW == 1 && VW == 1;
     static constexpr uint32_t BW = PAIRS && VW > KW ? VW : KW;  // words per buffer item
     static constexpr uint32_t KBUF = TILE * BW + PAD;    // words per key buffer
     static constexpr uint32_t IN_K = 0;
-    static constexpr uint32_t IN_V = IN_K + 2 * KBUF;
+    static constexpr uint32_t IN_V = IN_K + (PACKED ? 1 : 2) * KBUF;
     static constexpr uint32_t STG = IN_V + (PAIRS ? TILE * VW + PAD : 0);
-    static constexpr uint32_t WCNT = STG + TILE * KW;
+    static constexpr uint32_t WCNT = STG + TILE * (PACKED ? 2 : KW);
     static_assert(KBUF % 4 == 0 && (TILE * VW + PAD) % 4 == 0 && STG % KW == 0,
                   "input buffers 16-byte aligned for the bulk copies, stage aligned to keys");
+    static_assert(!PACKED || STG % 2 == 0, "packed stage 8-byte aligned");
     static constexpr uint32_t MASK = WCNT + WARPS * RADIX;
     static constexpr uint32_t WORDS = MASK + WARPS * RADIX;
     static constexpr size_t BYTES = WORDS * sizeof(uint32_t);
@@ -56,7 +63,8 @@ struct OnesweepSmem {
 // order per CTA): while tile i is ranked, the keys of tile i+1 are already
 // being copied into the other key buffer by the tensor memory accelerator
 // (one bulk copy, completing on an mbarrier); tile i+1's values follow as soon
-// as tile i's values have been staged.  A tile sits in its buffer at its
+// as tile i's values have been staged.  (32-bit pairs, PACKED: both of tile
+// i+1's copies start once tile i is ranked.)  A tile sits in its buffer at its
 // global 16-byte phase, so the bulk copy takes its aligned middle and at most
 // three items before and after it arrive by per-thread asynchronous copies on
 // the same barrier.  As soon as tile i+1's keys have landed its per-warp digit
@@ -91,7 +99,8 @@ struct OnesweepSmem {
 //     the earliest unfinished tile always progresses.  Every wait is bounded by
 //     spin_limit polls; when it runs out the kernel records ERR_TIMEOUT and
 //     CTAs that see the error write nothing more.
-//  4. Values are staged at the same positions (in the key buffer, free now).
+//  4. Values are staged at the same positions (in the key buffer, free now),
+//     or, for 32-bit pairs, were staged with their keys while ranking.
 //  5. Slot s of the staging buffer is stored to
 //       dst[G[b] + prefix_before_this_tile[b] + (s - tile_excl[b])],
 //     so consecutive threads store consecutive addresses of one bucket run.
@@ -128,6 +137,7 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
     static_assert(RADIX_BITS == 8, "digits are whole bytes of the key");
     constexpr uint32_t WARPS = L::WARPS;
     constexpr uint32_t TILE = L::TILE;
+    constexpr bool PACKED = L::PACKED;
     constexpr uint32_t WARP_ITEMS = 32 * ITEMS;
     constexpr int WIN = sizeof(S) == 8 ? WINDOW / 2 : WINDOW;  // same registers either way
     constexpr uint32_t LB_WARPS = RADIX / 32;                   // warps of the look-back
@@ -146,7 +156,10 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
     uint32_t* const smem = reinterpret_cast<uint32_t*>(s_dyn);
     K* const s_stage = reinterpret_cast<K*>(smem + L::STG);
     // Key buffer b (as K*), not yet skewed.
-    auto key_buf = [&](uint32_t b) { return reinterpret_cast<K*>(smem + L::IN_K + b * L::KBUF); };
+    auto key_buf = [&](uint32_t b) {
+        return reinterpret_cast<K*>(smem + L::IN_K + (PACKED ? 0u : b) * L::KBUF);
+    };
+    uint2* const s_stage2 = reinterpret_cast<uint2*>(smem + L::STG);  // PACKED: (key, value)
     uint32_t* const s_wcnt = smem + L::WCNT;
     const V* const s_in_v = reinterpret_cast<const V*>(smem + L::IN_V);
     __shared__ uint32_t s_gbase[RADIX];  // G[pass][b]
@@ -369,7 +382,8 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
         const uint4 geo = s_geo[it & 3];
         const uint4 ngeo = s_geo[(it + 1) & 3];
         const bool have_next = nxt < num_tiles;
-        if (have_next) issue_copy(key_buf(buf ^ 1), src_k, ngeo, &s_bar[buf ^ 1]);
+        if (!PACKED && have_next) issue_copy(key_buf(buf ^ 1), src_k, ngeo, &s_bar[buf ^ 1]);
+        if (PACKED) wait_bar(2);  // this tile's values, read while ranking
         // Segmented: this tile's bucket bases, fetched now, used after ranking.
         uint32_t seg_base = 0;
         if (SEG && tid < RADIX) seg_base = seg_gofs[((size_t)geo.w * PASSES + pass) * RADIX + tid];
@@ -416,7 +430,11 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
                 if (lane == first) before = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
                 before = __shfl_sync(0xffffffffu, before, first & 31u);
                 pos[j] = before + __popc(peers & lt);
-                if (is_live) s_stage[pos[j]] = k;
+                if constexpr (PACKED) {
+                    if (is_live) s_stage2[pos[j]] = make_uint2((uint32_t)k, (uint32_t)in_v[wofs + j * 32 + lane]);
+                } else {
+                    if (is_live) s_stage[pos[j]] = k;
+                }
             }
         };
         if (valid == TILE)
@@ -428,6 +446,10 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
         for (uint32_t i = lane; i < RADIX / 4; i += 32)
             reinterpret_cast<uint4*>(cnt)[i] = make_uint4(0, 0, 0, 0);
         __syncthreads();
+        if (PACKED && have_next) {  // both input buffers are free now
+            issue_copy(key_buf(buf ^ 1), src_k, ngeo, &s_bar[buf ^ 1]);
+            issue_copy(reinterpret_cast<V*>(smem + L::IN_V), src_v, ngeo, &s_bar[2]);
+        }
 
         // ---- 3. look-back (threads < 256) || count the next tile; values ----
         uint32_t next_id = 0;
@@ -515,7 +537,7 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
             }
         }
         // Every thread stages its own items' values (the key buffer is free).
-        if (PAIRS) {
+        if (PAIRS && !PACKED) {
             wait_bar(2);
             V vv[ITEMS];
 #pragma unroll
@@ -530,8 +552,11 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
             }
         }
         __syncthreads();
-        if (s_flag) break;  // an error somewhere: write nothing more (no copy is in flight)
-        if (PAIRS && have_next)
+        if (s_flag) {  // an error somewhere: write nothing more
+            if (PACKED && have_next) wait_bar(2);  // no copy is left in flight
+            break;
+        }
+        if (PAIRS && !PACKED && have_next)
             issue_copy(reinterpret_cast<V*>(smem + L::IN_V), src_v, ngeo, &s_bar[2]);
 
         // ---- 4. the next tile's counts, prefix and bases || this tile's stores
@@ -544,12 +569,14 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
             constexpr bool FULL = decltype(full)::value;
             auto store_slot = [&](uint32_t s) {
                 if (FULL || s < valid) {
-                    const K kk = s_stage[s];
+                    uint2 kv = make_uint2(0u, 0u);
+                    if constexpr (PACKED) kv = s_stage2[s];
+                    const K kk = PACKED ? (K)kv.x : s_stage[s];
                     const uint32_t g = s_gofs[digit_of(kk)] + s;
                     if (g < n) {
                         if constexpr (TYPED) dst_k[g] = key_from_ordered(kk, map_out);
                         else dst_k[g] = kk;
-                        if (PAIRS) dst_v[g] = in_kv[s];
+                        if (PAIRS) dst_v[g] = PACKED ? (V)kv.y : in_kv[s];
                     } else {
                         bad = true;
                     }
