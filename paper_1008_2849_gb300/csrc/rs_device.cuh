@@ -192,6 +192,13 @@ __device__ __forceinline__ void tma_load_1d(void* smem_dst, const void* gmem_src
         ::"r"(smem_u32(smem_dst)), "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
+// Start pulling `bytes` (a multiple of 16) from gmem_src (16-byte aligned)
+// into L2, without waiting; a later copy of the same bytes then hits L2.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* gmem_src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gmem_src), "r"(bytes)
+                 : "memory");
+}
+
 // Barrier among the first `count` threads of the CTA (count a multiple of
 // 32), on hardware barrier `id` (0 is the one __syncthreads uses).
 __device__ __forceinline__ void named_barrier_sync(uint32_t id, uint32_t count) {

@@ -272,6 +272,20 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
         }
     };
 
+    // One thread: start pulling tile g's aligned keys (and values) into L2,
+    // so that its bulk copies, issued later, hit L2.
+    auto prefetch_tile = [&](uint4 g) {
+        auto pf = [&](const auto* src) {
+            using T = std::remove_cv_t<std::remove_pointer_t<decltype(src)>>;
+            constexpr uint32_t PER16 = 16 / sizeof(T);
+            const uint32_t a0 = (PER16 - skew_of(src, g)) & (PER16 - 1);
+            const uint32_t nb = g.y > a0 ? ((g.y - a0) & ~(PER16 - 1)) : 0u;
+            if (nb) prefetch_l2_bulk(src + g.x + a0, nb * (uint32_t)sizeof(T));
+        };
+        pf(src_k);
+        if (PAIRS) pf(src_v);
+    };
+
     uint32_t phase = 0;  // bit b: parity of the next completion of s_bar[b]
     auto wait_bar = [&](uint32_t b) {
         uint32_t polls = 0;
@@ -520,6 +534,9 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
                 // anyone.
                 next_id = atomicAdd(&ctrl->tile_ctr[slot], 1u);
                 next_geo = load_geo(next_id);
+                // 32-bit pairs copy a tile in only once the tile before it is
+                // ranked: start pulling it into L2 an iteration earlier.
+                if (PACKED && next_id < num_tiles) prefetch_tile(next_geo);
             }
         }
         if (have_next) {
