@@ -41,7 +41,7 @@ void note_launch_end(int kind, cudaStream_t stream);
     X(0, 512, 16, 1, 32)    \
     X(1, 512, 8, 2, 16)     \
     X(2, 256, 16, 2, 32)    \
-    X(3, 384, 13, 2, 8)     \
+    X(3, 384, 13, 2, 6)     \
     X(4, 384, 12, 2, 8)     \
     X(5, 1024, 8, 1, 32)    \
     X(6, 384, 18, 2, 8)
