@@ -47,7 +47,8 @@ KEY_SEED = 2
 WORKLOAD = "sort_pairs_u32_2^28_uniform"
 ONESWEEP_SOURCES = ("paper_1008_2849_gb300/csrc/rs_onesweep.cuh",
                     "paper_1008_2849_gb300/csrc/rs_onesweep_launch.cuh",
-                    "paper_1008_2849_gb300/csrc/rs_device.cuh")
+                    "paper_1008_2849_gb300/csrc/rs_device.cuh",
+                    "paper_1008_2849_gb300/csrc/rs_internal.h")  # tile shapes
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pairs_2^28_traffic.txt")
 
 
