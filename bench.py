@@ -10,9 +10,11 @@ Every step sorts its own freshly copied input (2 GiB, far larger than the
 
 Printed (rank 0, one JSON line): pairs/s for the whole job; the dominant
 kernel's achieved HBM bandwidth against the measured copy peak (roofline);
-the same metric end to end through rs_sort_pairs_host with pinned host
-buffers (copies included); the CPU oracle's throughput on a bounded sample
-(cpu_baseline); SM clocks sampled during the timed region.
+the same metric end to end through rs_sort_pairs_host_batch with pinned host
+buffers (every step's upload and download included, overlapping the sorts of
+neighbouring steps), next to one rs_sort_pairs_host call per array; the CPU
+oracle's throughput on a bounded sample (cpu_baseline); SM clocks sampled
+during the timed region.
 
 With N > 1 (torchrun), every rank sorts its own independent 2^28-pair array
 (replicas: the sort of one array does not shard without an exchange step),
@@ -121,9 +123,11 @@ def recorded_traffic():
 
 def link_bandwidths(host_buf, dev, reps: int = 3):
     """Host->device and device->host GB/s of plain copies of `host_buf`
-    (pinned) on this rank's GPU: the best of `reps` timed copies each."""
+    (pinned) on this rank's GPU, the best of `reps` timed copies each, and
+    the seconds that one copy each way takes when both run at once."""
     import torch
     d = torch.empty_like(host_buf, device=dev)
+    d2 = torch.empty_like(d)
     back = torch.empty_like(host_buf).pin_memory()
     nbytes = host_buf.numel() * host_buf.element_size()
     out = []
@@ -136,7 +140,18 @@ def link_bandwidths(host_buf, dev, reps: int = 3):
             torch.cuda.synchronize(dev)
             best = min(best, time.perf_counter() - t0)
         out.append(nbytes / best / 1e9)
-    return out[0], out[1]
+    s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    duplex = float("inf")
+    for _ in range(reps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s_up):
+            d.copy_(host_buf, non_blocking=True)
+        with torch.cuda.stream(s_down):
+            back.copy_(d2, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        duplex = min(duplex, time.perf_counter() - t0)
+    return out[0], out[1], duplex
 
 
 def host_cpu_model() -> str:
@@ -320,29 +335,54 @@ def main():
 
     e2e = None
     if not args.no_e2e:
+        # Host arrays in pinned memory; every step uploads its input, sorts it
+        # and downloads its result.  One rs_sort_pairs_host_batch call runs
+        # all steps with two device buffer sets, so that step i+1's upload
+        # and step i-1's download overlap step i's sort.
         kin = torch.from_numpy(k_host.view(np.int32)).pin_memory()
         vin = torch.from_numpy(v_host.view(np.int32)).pin_memory()
-        kout = torch.empty_like(kin).pin_memory()
-        vout = torch.empty_like(vin).pin_memory()
-        for _ in range(2):
-            rs.sort_pairs_host(kin, vin, kout, vout)
+        outs = [(torch.empty_like(kin).pin_memory(), torch.empty_like(vin).pin_memory())
+                for _ in range(2)]
+
+        def host_batch(steps):
+            rs.sort_pairs_host_batch([kin] * steps, [vin] * steps,
+                                     [outs[i % 2][0] for i in range(steps)],
+                                     [outs[i % 2][1] for i in range(steps)])
+        host_batch(2)
         e2e_steps = max(3, min(args.steps, 10))
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            rs.sort_pairs_host(kin, vin, kout, vout)
+        host_batch(e2e_steps)
         dt = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e = {"value": job_throughput(world, e2e_steps, n, dt), "unit": UNIT,
                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
-               "api": "rs_sort_pairs_host (pinned host buffers)", "steps": e2e_steps}
-        # The host link bounds this number: time the same bytes through plain
-        # pinned copies, and compare with copies + the device-timed sort in series.
-        h2d, d2h = link_bandwidths(kin, dev)
-        bound_s = 8 * n / (h2d * 1e9) + 8 * n / (d2h * 1e9) + elapsed_ms / 1e3 / args.steps
+               "api": "rs_sort_pairs_host_batch (pinned host buffers, all steps in one call)",
+               "steps": e2e_steps}
+        # For comparison: one synchronous rs_sort_pairs_host call per array.
+        rs.sort_pairs_host(kin, vin, outs[0][0], outs[0][1])
+        serial_steps = 3
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(serial_steps):
+            rs.sort_pairs_host(kin, vin, outs[0][0], outs[0][1])
+        dt1 = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e["one_call_per_array"] = {"value": job_throughput(world, serial_steps, n, dt1),
+                                     "api": "rs_sort_pairs_host"}
+        # The host link bounds these numbers: time the same bytes through
+        # plain pinned copies.  One array at a time, copies and the
+        # device-timed sort run in series; pipelined, a step needs at least
+        # the longer of the sort and one upload with one download at once.
+        del outs
+        h2d, d2h, duplex_half = link_bandwidths(kin, dev)
+        sort_s = elapsed_ms / 1e3 / args.steps
+        serial_s = 8 * n / (h2d * 1e9) + 8 * n / (d2h * 1e9) + sort_s
+        pipe_s = max(2 * duplex_half, sort_s)  # keys and values: two copies each way
         e2e.update({"link_h2d_gbs": h2d, "link_d2h_gbs": d2h,
-                    "serial_bound": n / bound_s,
-                    "frac_of_serial_bound": (e2e["value"] / world) / (n / bound_s)})
+                    "link_gbs_each_way_at_once": 4 * n / duplex_half / 1e9,
+                    "serial_bound": n / serial_s, "pipelined_bound": n / pipe_s,
+                    "frac_of_pipelined_bound": (e2e["value"] / world) / (n / pipe_s)})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -206,6 +206,22 @@ rs_status rs_digit_histograms_ex(const uint32_t* d_keys, size_t n, uint32_t* d_h
 rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in,
                              uint32_t* h_keys_out, uint32_t* h_vals_out, size_t n);
 
+/* Pipelined end-to-end sorts of `count` independent HOST arrays: array i
+ * (h_keys_in[i] and, if h_vals_in is not NULL, h_vals_in[i]; n[i] items) is
+ * copied to the device, sorted as by rs_sort_pairs (or rs_sort_keys when
+ * h_vals_in is NULL), and copied back to h_keys_out[i] (h_vals_out[i]).
+ * Two device buffer sets alternate, so that array i+1's upload and array
+ * i-1's download run while array i is sorted: the host link carries both
+ * directions at once.  Every array's copies are still complete copies; the
+ * call returns when all arrays are back.  Inputs are not modified; an output
+ * may be its own input; arrays with n[i] = 0 are skipped.  Pinned host
+ * memory gives full link bandwidth.  Device buffers are cached inside the
+ * library.  Synchronous.  n[i] >= 2^32 is RS_ERR_UNSUPPORTED; NULL tables or
+ * entries are RS_ERR_INVALID_ARG. */
+rs_status rs_sort_pairs_host_batch(const uint32_t* const* h_keys_in,
+                                   const uint32_t* const* h_vals_in, uint32_t* const* h_keys_out,
+                                   uint32_t* const* h_vals_out, const size_t* n, uint32_t count);
+
 /* ---- captured sorts (CUDA graphs) -----------------------------------------
  * A sort of fixed device buffers captured once into a CUDA graph and then
  * replayed with one launch: the batched form for serving loops that refill

@@ -35,6 +35,15 @@ struct DevState {
     size_t h_cap = 0;
     cudaStream_t s_main = nullptr, s_side = nullptr;
     cudaEvent_t ev_vals = nullptr, ev_sorted = nullptr, ev_side_done = nullptr;
+    // the pipelined host-buffer path: two device buffer sets, a copy-in and a
+    // copy-out stream (sorts run on s_main), and per set the events that
+    // order them
+    uint32_t* bk[2] = {nullptr, nullptr};
+    uint32_t* bv[2] = {nullptr, nullptr};
+    size_t b_cap = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done_sort[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
 };
 DevState g_dev[kMaxDevices];
 std::mutex g_mu;       // guards the buffers of g_dev and serialises the plain calls
@@ -479,6 +488,96 @@ rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_i
     if (cudaMemcpyAsync(h_keys_out, d.hk, bytes, cudaMemcpyDeviceToHost, d.s_main) != cudaSuccess)
         return RS_ERR_CUDA;
     if (cudaStreamSynchronize(d.s_side) != cudaSuccess) return RS_ERR_CUDA;
+    return sticky_status(d.s_main);
+}
+
+rs_status rs_sort_pairs_host_batch(const uint32_t* const* h_keys_in,
+                                   const uint32_t* const* h_vals_in, uint32_t* const* h_keys_out,
+                                   uint32_t* const* h_vals_out, const size_t* n, uint32_t count) {
+    if (count == 0) return RS_OK;
+    if (!h_keys_in || !h_keys_out || !n || (h_vals_in && !h_vals_out)) return RS_ERR_INVALID_ARG;
+    const bool pairs = h_vals_in != nullptr;
+    size_t nmax = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (n[i] >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
+        if (n[i] == 0) continue;
+        if (!h_keys_in[i] || !h_keys_out[i] || (pairs && (!h_vals_in[i] || !h_vals_out[i])))
+            return RS_ERR_INVALID_ARG;
+        if (n[i] > nmax) nmax = n[i];
+    }
+    if (nmax == 0) return RS_OK;
+    std::lock_guard<std::mutex> lock(g_mu);
+    const int dev = current_device();
+    if (dev < 0) return RS_ERR_CUDA;
+    DeviceInfo di;
+    rs_status st = device_info_for(dev, &di);
+    if (st != RS_OK) return st;
+    DevState& d = g_dev[dev];
+    if (!d.s_main) {
+        if (cudaStreamCreateWithFlags(&d.s_main, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&d.s_side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d.ev_vals, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d.ev_sorted, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&d.ev_side_done, cudaEventDisableTiming) != cudaSuccess)
+            return RS_ERR_CUDA;
+    }
+    if (!d.s_in) {
+        if (cudaStreamCreateWithFlags(&d.s_in, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&d.s_out, cudaStreamNonBlocking) != cudaSuccess)
+            return RS_ERR_CUDA;
+        for (int b = 0; b < 2; ++b)
+            if (cudaEventCreateWithFlags(&d.ev_in[b], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&d.ev_done_sort[b], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&d.ev_out[b], cudaEventDisableTiming) != cudaSuccess)
+                return RS_ERR_CUDA;
+    }
+    if (d.b_cap < nmax) {
+        for (int b = 0; b < 2; ++b) {
+            if (d.bk[b]) cudaFree(d.bk[b]);
+            if (d.bv[b]) cudaFree(d.bv[b]);
+            d.bk[b] = d.bv[b] = nullptr;
+        }
+        d.b_cap = 0;
+        for (int b = 0; b < 2; ++b)
+            if (cudaMalloc(&d.bk[b], nmax * 4) != cudaSuccess ||
+                cudaMalloc(&d.bv[b], nmax * 4) != cudaSuccess) {
+                cudaGetLastError();
+                return RS_ERR_OUT_OF_MEMORY;
+            }
+        d.b_cap = nmax;
+    }
+    st = ensure_workspace_locked(d, layout_for(nmax, pairs).total);
+    if (st != RS_OK) return st;
+    // Array i uses buffer set i % 2.  Its upload waits for the download of
+    // array i - 2 (same set); its sort (one compute stream, one workspace)
+    // waits for its upload; its download waits for its sort.  So array i+1's
+    // upload and array i-1's download run while array i is sorted.
+    for (uint32_t i = 0; i < count; ++i) {
+        if (n[i] == 0) continue;
+        const int b = (int)(i & 1);
+        const size_t bytes = n[i] * 4;
+        if (cudaStreamWaitEvent(d.s_in, d.ev_out[b], 0) != cudaSuccess ||
+            cudaMemcpyAsync(d.bk[b], h_keys_in[i], bytes, cudaMemcpyHostToDevice, d.s_in) !=
+                cudaSuccess ||
+            (pairs && cudaMemcpyAsync(d.bv[b], h_vals_in[i], bytes, cudaMemcpyHostToDevice,
+                                      d.s_in) != cudaSuccess) ||
+            cudaEventRecord(d.ev_in[b], d.s_in) != cudaSuccess ||
+            cudaStreamWaitEvent(d.s_main, d.ev_in[b], 0) != cudaSuccess)
+            return RS_ERR_CUDA;
+        st = enqueue_sort(d.bk[b], pairs ? d.bv[b] : nullptr, (uint32_t)n[i], d.s_main, d.ws,
+                          d.ws_bytes);
+        if (st != RS_OK) return st;
+        if (cudaEventRecord(d.ev_done_sort[b], d.s_main) != cudaSuccess ||
+            cudaStreamWaitEvent(d.s_out, d.ev_done_sort[b], 0) != cudaSuccess ||
+            cudaMemcpyAsync(h_keys_out[i], d.bk[b], bytes, cudaMemcpyDeviceToHost, d.s_out) !=
+                cudaSuccess ||
+            (pairs && cudaMemcpyAsync(h_vals_out[i], d.bv[b], bytes, cudaMemcpyDeviceToHost,
+                                      d.s_out) != cudaSuccess) ||
+            cudaEventRecord(d.ev_out[b], d.s_out) != cudaSuccess)
+            return RS_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(d.s_out) != cudaSuccess || cudaStreamSynchronize(d.s_in) != cudaSuccess)
+        return RS_ERR_CUDA;
     return sticky_status(d.s_main);
 }
 

@@ -53,6 +53,7 @@ SIGNATURES = {
     "rs_status_string": (ctypes.c_char_p, [_int]),
     "rs_digit_histograms_ex": (_int, [_vp, _sz, _vp, _vp]),
     "rs_sort_pairs_host": (_int, [_vp, _vp, _vp, _vp, _sz]),
+    "rs_sort_pairs_host_batch": (_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_uint32]),
     "rs_sort_pairs_noalloc": (_int, [_vp, _vp, _sz, _vp]),
     "rs_launch_count": (ctypes.c_uint64, []),
     "rs_profile_enable": (_int, [_int]),
@@ -325,21 +326,44 @@ def digit_histograms(keys, out=None, stream=None):
     return out
 
 
+def _host_ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or a.element_size() != 4 or not a.is_contiguous():
+            raise ValueError("host tensors must be contiguous CPU tensors of 4-byte ints")
+        return a.data_ptr()
+    if a.dtype.itemsize != 4 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be contiguous 4-byte ints")
+    return a.ctypes.data
+
+
+def _host_len(a) -> int:
+    return a.numel() if hasattr(a, "numel") else a.size
+
+
 def sort_pairs_host(keys_in, vals_in, keys_out, vals_out) -> None:
     """End-to-end sort of host arrays (numpy or CPU torch; pinned is fastest)."""
-    def hp(a):
-        if a is None:
-            return None
-        if hasattr(a, "data_ptr"):
-            if a.is_cuda or a.element_size() != 4 or not a.is_contiguous():
-                raise ValueError("host tensors must be contiguous CPU tensors of 4-byte ints")
-            return a.data_ptr()
-        if a.dtype.itemsize != 4 or not a.flags["C_CONTIGUOUS"]:
-            raise ValueError("host arrays must be contiguous 4-byte ints")
-        return a.ctypes.data
-    n = keys_in.numel() if hasattr(keys_in, "numel") else keys_in.size
-    _check(lib().rs_sort_pairs_host(hp(keys_in), hp(vals_in), hp(keys_out), hp(vals_out), n),
+    _check(lib().rs_sort_pairs_host(_host_ptr(keys_in), _host_ptr(vals_in), _host_ptr(keys_out),
+                                    _host_ptr(vals_out), _host_len(keys_in)),
            "rs_sort_pairs_host")
+
+
+def sort_pairs_host_batch(keys_in, vals_in, keys_out, vals_out) -> None:
+    """Pipelined end-to-end sorts of several host arrays (lists of equal
+    length; vals_in / vals_out None for keys only): the next array's upload
+    and the previous one's download overlap the current sort."""
+    count = len(keys_in)
+    if len(keys_out) != count or (vals_in is not None and
+                                  (len(vals_in) != count or len(vals_out) != count)):
+        raise ValueError("input and output lists differ in length")
+    P = ctypes.c_void_p * max(count, 1)
+    ki = P(*[_host_ptr(a) for a in keys_in])
+    ko = P(*[_host_ptr(a) for a in keys_out])
+    vi = None if vals_in is None else P(*[_host_ptr(a) for a in vals_in])
+    vo = None if vals_out is None else P(*[_host_ptr(a) for a in vals_out])
+    n = (ctypes.c_size_t * max(count, 1))(*[_host_len(a) for a in keys_in])
+    _check(lib().rs_sort_pairs_host_batch(ki, vi, ko, vo, n, count), "rs_sort_pairs_host_batch")
 
 
 NOALLOC_MAX_ITEMS = 1 << 20

@@ -83,6 +83,14 @@ def test_host_side_argument_errors(lib):
     assert lib.rs_sort_pairs_ex(ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), 100, None, None, 0) == 1
     assert lib.rs_digit_histograms_ex(ctypes.c_void_p(4096), 10, None, None) == 1
     assert lib.rs_sort_pairs_host(None, None, None, None, 10) == 1
+    assert lib.rs_sort_pairs_host_batch(None, None, None, None, None, 0) == 0   # nothing to do
+    assert lib.rs_sort_pairs_host_batch(None, None, None, None, None, 2) == 1   # no tables
+    P = ctypes.c_void_p * 2
+    tab = P(4096, None)
+    sizes = (ctypes.c_size_t * 2)(10, 10)
+    assert lib.rs_sort_pairs_host_batch(tab, None, tab, None, sizes, 2) == 1   # a NULL entry
+    big = (ctypes.c_size_t * 2)(1 << 32, 0)
+    assert lib.rs_sort_pairs_host_batch(tab, None, tab, None, big, 2) == 5     # n >= 2^32
 
 
 def test_workspace_bytes_kv(lib):

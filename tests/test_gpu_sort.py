@@ -173,6 +173,31 @@ def test_host_buffers_end_to_end(rs):
     assert np.array_equal(kk, oracle.sort_keys(k))
 
 
+def test_host_batch_end_to_end(rs):
+    """Pipelined host sorts: arrays of different sizes (one empty, several
+    sharing the two device buffer sets in turn), pairs in pinned memory and
+    keys only in pageable memory with outputs over the inputs; every array
+    equals the oracle's sort of it alone."""
+    import torch
+    sizes = [1_000_003, 0, 5, 8192, 2_500_001, 70_001, 1]
+    ks = [inputs.keys("and2" if i % 2 else "uniform", m, seed=80 + i) for i, m in enumerate(sizes)]
+    vs = [inputs.index_values(m) for m in sizes]
+    kin = [torch.from_numpy(k.view(np.int32)).pin_memory() for k in ks]
+    vin = [torch.from_numpy(v.view(np.int32)).pin_memory() for v in vs]
+    kout = [torch.empty_like(t).pin_memory() for t in kin]
+    vout = [torch.empty_like(t).pin_memory() for t in vin]
+    rs.sort_pairs_host_batch(kin, vin, kout, vout)
+    for i, m in enumerate(sizes):
+        ko, vo = oracle_sort(ks[i], vs[i])
+        assert np.array_equal(kout[i].numpy().view(np.uint32), ko), i
+        assert np.array_equal(vout[i].numpy().view(np.uint32), vo), i
+        assert np.array_equal(kin[i].numpy().view(np.uint32), ks[i])  # inputs untouched
+    kk = [k.copy() for k in ks]
+    rs.sort_pairs_host_batch(kk, None, kk, None)
+    for i in range(len(sizes)):
+        assert np.array_equal(kk[i], oracle.sort_keys(ks[i])), i
+
+
 def test_lookback_wait_runs_out(rs):
     """The first tile withholds its counts, so later tiles' bounded waits run
     out: the call reports RS_ERR_TIMEOUT and the context stays usable."""
