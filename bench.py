@@ -337,7 +337,7 @@ def main():
     if not args.no_e2e:
         # Host arrays in pinned memory; every step uploads its input, sorts it
         # and downloads its result.  One rs_sort_pairs_host_batch call runs
-        # all steps with two device buffer sets, so that step i+1's upload
+        # all steps with rotating device buffer sets, so that step i+1's upload
         # and step i-1's download overlap step i's sort.
         kin = torch.from_numpy(k_host.view(np.int32)).pin_memory()
         vin = torch.from_numpy(v_host.view(np.int32)).pin_memory()

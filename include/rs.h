@@ -210,7 +210,7 @@ rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_i
  * (h_keys_in[i] and, if h_vals_in is not NULL, h_vals_in[i]; n[i] items) is
  * copied to the device, sorted as by rs_sort_pairs (or rs_sort_keys when
  * h_vals_in is NULL), and copied back to h_keys_out[i] (h_vals_out[i]).
- * Two device buffer sets alternate, so that array i+1's upload and array
+ * Three device buffer sets rotate, so that array i+1's upload and array
  * i-1's download run while array i is sorted: the host link carries both
  * directions at once.  Every array's copies are still complete copies; the
  * call returns when all arrays are back.  Inputs are not modified; an output

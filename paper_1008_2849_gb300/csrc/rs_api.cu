@@ -20,6 +20,9 @@ namespace {
 
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 constexpr int kMaxDevices = 64;
+// Device buffer sets of rs_sort_pairs_host_batch: with three, an array's
+// upload never waits for the download of the array two before it.
+constexpr int kHostSets = 3;
 
 std::atomic<uint64_t> g_launches{0};
 
@@ -35,15 +38,14 @@ struct DevState {
     size_t h_cap = 0;
     cudaStream_t s_main = nullptr, s_side = nullptr;
     cudaEvent_t ev_vals = nullptr, ev_sorted = nullptr, ev_side_done = nullptr;
-    // the pipelined host-buffer path: two device buffer sets, a copy-in and a
-    // copy-out stream (sorts run on s_main), and per set the events that
-    // order them
-    uint32_t* bk[2] = {nullptr, nullptr};
-    uint32_t* bv[2] = {nullptr, nullptr};
+    // the pipelined host-buffer path: kHostSets device buffer sets, a
+    // copy-in and a copy-out stream (sorts run on s_main), and per set the
+    // events that order them
+    uint32_t* bk[kHostSets] = {};
+    uint32_t* bv[kHostSets] = {};
     size_t b_cap = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done_sort[2] = {nullptr, nullptr},
-                ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[kHostSets] = {}, ev_done_sort[kHostSets] = {}, ev_out[kHostSets] = {};
 };
 DevState g_dev[kMaxDevices];
 std::mutex g_mu;       // guards the buffers of g_dev and serialises the plain calls
@@ -525,20 +527,20 @@ rs_status rs_sort_pairs_host_batch(const uint32_t* const* h_keys_in,
         if (cudaStreamCreateWithFlags(&d.s_in, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&d.s_out, cudaStreamNonBlocking) != cudaSuccess)
             return RS_ERR_CUDA;
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < kHostSets; ++b)
             if (cudaEventCreateWithFlags(&d.ev_in[b], cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&d.ev_done_sort[b], cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&d.ev_out[b], cudaEventDisableTiming) != cudaSuccess)
                 return RS_ERR_CUDA;
     }
     if (d.b_cap < nmax) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kHostSets; ++b) {
             if (d.bk[b]) cudaFree(d.bk[b]);
             if (d.bv[b]) cudaFree(d.bv[b]);
             d.bk[b] = d.bv[b] = nullptr;
         }
         d.b_cap = 0;
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < kHostSets; ++b)
             if (cudaMalloc(&d.bk[b], nmax * 4) != cudaSuccess ||
                 cudaMalloc(&d.bv[b], nmax * 4) != cudaSuccess) {
                 cudaGetLastError();
@@ -548,13 +550,14 @@ rs_status rs_sort_pairs_host_batch(const uint32_t* const* h_keys_in,
     }
     st = ensure_workspace_locked(d, layout_for(nmax, pairs).total);
     if (st != RS_OK) return st;
-    // Array i uses buffer set i % 2.  Its upload waits for the download of
-    // array i - 2 (same set); its sort (one compute stream, one workspace)
-    // waits for its upload; its download waits for its sort.  So array i+1's
-    // upload and array i-1's download run while array i is sorted.
+    // Array i uses buffer set i % kHostSets.  Its upload waits for the
+    // download of the array that used the set before; its sort (one compute
+    // stream, one workspace) waits for its upload; its download waits for its
+    // sort.  So the next array's upload and the previous one's download run
+    // while array i is sorted.
     for (uint32_t i = 0; i < count; ++i) {
         if (n[i] == 0) continue;
-        const int b = (int)(i & 1);
+        const int b = (int)(i % kHostSets);
         const size_t bytes = n[i] * 4;
         if (cudaStreamWaitEvent(d.s_in, d.ev_out[b], 0) != cudaSuccess ||
             cudaMemcpyAsync(d.bk[b], h_keys_in[i], bytes, cudaMemcpyHostToDevice, d.s_in) !=

@@ -175,11 +175,11 @@ def test_host_buffers_end_to_end(rs):
 
 def test_host_batch_end_to_end(rs):
     """Pipelined host sorts: arrays of different sizes (one empty, several
-    sharing the two device buffer sets in turn), pairs in pinned memory and
+    taking the device buffer sets in turn), pairs in pinned memory and
     keys only in pageable memory with outputs over the inputs; every array
     equals the oracle's sort of it alone."""
     import torch
-    sizes = [1_000_003, 0, 5, 8192, 2_500_001, 70_001, 1]
+    sizes = [1_000_003, 0, 5, 8192, 2_500_001, 70_001, 1, 300_007]
     ks = [inputs.keys("and2" if i % 2 else "uniform", m, seed=80 + i) for i, m in enumerate(sizes)]
     vs = [inputs.index_values(m) for m in sizes]
     kin = [torch.from_numpy(k.view(np.int32)).pin_memory() for k in ks]
