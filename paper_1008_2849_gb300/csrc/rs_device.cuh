@@ -71,6 +71,15 @@ constexpr uint32_t KEY_F32 = 2;
 constexpr uint32_t KEY_U64 = 3;
 constexpr uint32_t KEY_I64 = 4;
 constexpr uint32_t KEY_F64 = 5;
+// Typed sorts launch two instances of a scatter pass: one without the key
+// maps, for the passes that move ordered words only, and one with them, for
+// the first and the last executed pass.  Which passes those are is known on
+// the device (the pass plan), so each instance returns at once unless the
+// pass is its own; these bits, added to the key type argument, say which
+// instance a launch is.
+constexpr uint32_t ROLE_PLAIN_PASSES = 1u << 8;
+constexpr uint32_t ROLE_MAP_PASSES = 1u << 9;
+constexpr uint32_t KEY_TYPE_MASK = 0xffu;
 
 __device__ __forceinline__ uint32_t key_to_ordered(uint32_t k, uint32_t type) {
     const uint32_t neg = type == KEY_F32 ? (uint32_t)((int32_t)k >> 31) : 0u;

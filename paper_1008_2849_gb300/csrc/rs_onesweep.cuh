@@ -180,6 +180,20 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+    if (key_type & (ROLE_PLAIN_PASSES | ROLE_MAP_PASSES)) {
+        // One of the two instances of a typed sort's pass: keep the pass if
+        // it is this instance's (an executed first or last pass needs the
+        // maps; every other pass, skipped ones included, does not).
+        bool first = true, last = true;
+        for (uint32_t q = 0; q < NPASS; ++q) {
+            if (ctrl->dir[q] == DIR_SKIP) continue;
+            if (q < pass) first = false;
+            if (q > pass) last = false;
+        }
+        const bool maps = ctrl->dir[slot] != DIR_SKIP && (first || last);
+        if (maps != ((key_type & ROLE_MAP_PASSES) != 0)) return;
+        key_type &= KEY_TYPE_MASK;
+    }
     if (SEG) {
         if (ld_relaxed(&ctrl->err) != 0) return;  // malformed segment table: no work
         num_tiles = ctrl->seg_tiles;

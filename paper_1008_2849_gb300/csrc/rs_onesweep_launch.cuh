@@ -65,10 +65,17 @@ static rs_status launch_onesweep_variant(int cfg, uint32_t* ka, uint32_t* va, ui
                                          const SegView& seg, uint32_t key_type,
                                          cudaStream_t stream) {
     if (key_type != KEY_U32) {
+        // Typed keys: the passes that need no maps run without them (see
+        // ROLE_PLAIN_PASSES); both instances are launched for every pass.
         using T = TileShape<kTypedShape>;
+        const rs_status st =
+            launch_onesweep_shape<T::threads, T::items, T::min_blocks, T::window, PAIRS, S, SEG,
+                                  false>(ka, va, kb, vb, n, pass, slot, ctrl, sticky, status,
+                                         status_clear, seg, key_type | ROLE_PLAIN_PASSES, stream);
+        if (st != RS_OK) return st;
         return launch_onesweep_shape<T::threads, T::items, T::min_blocks, T::window, PAIRS, S, SEG,
                                      true>(ka, va, kb, vb, n, pass, slot, ctrl, sticky, status,
-                                           status_clear, seg, key_type, stream);
+                                           status_clear, seg, key_type | ROLE_MAP_PASSES, stream);
     }
     switch (cfg) {
 #define RS_CASE(I, T, J, B, W)                                                                    \

@@ -31,8 +31,14 @@ rs_status pass64_typed(unsigned long long* ka, V* va, unsigned long long* kb, V*
     if (key_type == KEY_U64)
         return pass64<PAIRS, V, S, false>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
                                           status_clear, KEY_U32, stream);
+    // Typed keys: the passes that need no maps run without them (see
+    // ROLE_PLAIN_PASSES); both instances are launched for every pass.
+    const rs_status st = pass64<PAIRS, V, S, false>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
+                                                    status_clear, key_type | ROLE_PLAIN_PASSES,
+                                                    stream);
+    if (st != RS_OK) return st;
     return pass64<PAIRS, V, S, true>(ka, va, kb, vb, n, pass, ctrl, sticky, status, status_clear,
-                                     key_type, stream);
+                                     key_type | ROLE_MAP_PASSES, stream);
 }
 
 template <typename S>
