@@ -469,27 +469,34 @@ rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_i
     st = ensure_workspace_locked(d, layout_for(n, pairs).total);
     if (st != RS_OK) return st;
     const size_t bytes = n * 4;
+    // A failure part-way waits for the work already enqueued, so that no copy
+    // still reads or writes the caller's arrays.
+    auto drain = [&](rs_status e) {
+        cudaStreamSynchronize(d.s_side);
+        cudaStreamSynchronize(d.s_main);
+        return e;
+    };
     // Keys first on the main stream (the histogram needs them); values on
     // the side stream, overlapping the histogram and plan kernels.
     if (cudaMemcpyAsync(d.hk, h_keys_in, bytes, cudaMemcpyHostToDevice, d.s_main) != cudaSuccess)
-        return RS_ERR_CUDA;
+        return drain(RS_ERR_CUDA);
     if (pairs) {
         if (cudaMemcpyAsync(d.hv, h_vals_in, bytes, cudaMemcpyHostToDevice, d.s_side) != cudaSuccess ||
             cudaEventRecord(d.ev_vals, d.s_side) != cudaSuccess ||
             cudaStreamWaitEvent(d.s_main, d.ev_vals, 0) != cudaSuccess)
-            return RS_ERR_CUDA;
+            return drain(RS_ERR_CUDA);
     }
     st = enqueue_sort(d.hk, pairs ? d.hv : nullptr, (uint32_t)n, d.s_main, d.ws, d.ws_bytes);
-    if (st != RS_OK) return st;
+    if (st != RS_OK) return drain(st);
     if (pairs) {
         if (cudaEventRecord(d.ev_sorted, d.s_main) != cudaSuccess ||
             cudaStreamWaitEvent(d.s_side, d.ev_sorted, 0) != cudaSuccess ||
             cudaMemcpyAsync(h_vals_out, d.hv, bytes, cudaMemcpyDeviceToHost, d.s_side) != cudaSuccess)
-            return RS_ERR_CUDA;
+            return drain(RS_ERR_CUDA);
     }
     if (cudaMemcpyAsync(h_keys_out, d.hk, bytes, cudaMemcpyDeviceToHost, d.s_main) != cudaSuccess)
-        return RS_ERR_CUDA;
-    if (cudaStreamSynchronize(d.s_side) != cudaSuccess) return RS_ERR_CUDA;
+        return drain(RS_ERR_CUDA);
+    if (cudaStreamSynchronize(d.s_side) != cudaSuccess) return drain(RS_ERR_CUDA);
     return sticky_status(d.s_main);
 }
 
@@ -554,7 +561,14 @@ rs_status rs_sort_pairs_host_batch(const uint32_t* const* h_keys_in,
     // download of the array that used the set before; its sort (one compute
     // stream, one workspace) waits for its upload; its download waits for its
     // sort.  So the next array's upload and the previous one's download run
-    // while array i is sorted.
+    // while array i is sorted.  A failure part-way waits for the work already
+    // enqueued, so that no copy still reads or writes the caller's arrays.
+    auto drain = [&](rs_status e) {
+        cudaStreamSynchronize(d.s_in);
+        cudaStreamSynchronize(d.s_main);
+        cudaStreamSynchronize(d.s_out);
+        return e;
+    };
     for (uint32_t i = 0; i < count; ++i) {
         if (n[i] == 0) continue;
         const int b = (int)(i % kHostSets);
@@ -566,10 +580,10 @@ rs_status rs_sort_pairs_host_batch(const uint32_t* const* h_keys_in,
                                       d.s_in) != cudaSuccess) ||
             cudaEventRecord(d.ev_in[b], d.s_in) != cudaSuccess ||
             cudaStreamWaitEvent(d.s_main, d.ev_in[b], 0) != cudaSuccess)
-            return RS_ERR_CUDA;
+            return drain(RS_ERR_CUDA);
         st = enqueue_sort(d.bk[b], pairs ? d.bv[b] : nullptr, (uint32_t)n[i], d.s_main, d.ws,
                           d.ws_bytes);
-        if (st != RS_OK) return st;
+        if (st != RS_OK) return drain(st);
         if (cudaEventRecord(d.ev_done_sort[b], d.s_main) != cudaSuccess ||
             cudaStreamWaitEvent(d.s_out, d.ev_done_sort[b], 0) != cudaSuccess ||
             cudaMemcpyAsync(h_keys_out[i], d.bk[b], bytes, cudaMemcpyDeviceToHost, d.s_out) !=
@@ -577,10 +591,10 @@ rs_status rs_sort_pairs_host_batch(const uint32_t* const* h_keys_in,
             (pairs && cudaMemcpyAsync(h_vals_out[i], d.bv[b], bytes, cudaMemcpyDeviceToHost,
                                       d.s_out) != cudaSuccess) ||
             cudaEventRecord(d.ev_out[b], d.s_out) != cudaSuccess)
-            return RS_ERR_CUDA;
+            return drain(RS_ERR_CUDA);
     }
     if (cudaStreamSynchronize(d.s_out) != cudaSuccess || cudaStreamSynchronize(d.s_in) != cudaSuccess)
-        return RS_ERR_CUDA;
+        return drain(RS_ERR_CUDA);
     return sticky_status(d.s_main);
 }
 
