@@ -82,7 +82,8 @@ struct OnesweepSmem {
 //  2. Ranking (per warp, item slot j at a time): the lanes holding the same
 //     digit come from one ballot per digit bit (odd slots) or from a shared
 //     peer mask each lane ORs its bit into (even slots) -- alternating keeps
-//     both the integer and the shared-memory pipes busy; the lowest lane of the
+//     both the integer and the shared-memory pipes busy, and an odd slot's
+//     ballots run while the even slot before it waits for its mask; the lowest lane of the
 //     group adds the group's size to the warp's position counter of the digit;
 //     an item's tile position is the counter's old value plus the number of its
 //     peers on lower lanes.  The key is written straight to that position of
@@ -441,23 +442,7 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
             constexpr bool FULL = decltype(full)::value;
             const uint32_t left = FULL ? WARP_ITEMS : (valid > wofs ? valid - wofs : 0u);
             const K* keys = in_k + wofs + lane;
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const bool is_live = FULL || j * 32 + lane < left;
-                const uint32_t live = FULL ? 0xffffffffu : prefix_lanes(j * 32, left);
-                const K k = read_key(keys[j * 32]);
-                const uint32_t d = digit_of(k);
-                uint32_t peers;
-                if (j & 1) {
-                    peers = match_label<RADIX_BITS>(d) & live;  // integer pipe
-                } else {
-                    __syncwarp();                                // shared-memory pipe
-                    if (is_live) atomicOr(&mask[d], 1u << lane);
-                    __syncwarp();
-                    peers = is_live ? mask[d] : 0u;
-                    __syncwarp();
-                    if (is_live && (peers & lt) == 0) mask[d] = 0;
-                }
+            auto finish = [&](int j, K k, uint32_t d, uint32_t peers, bool is_live) {
                 const uint32_t first = __ffs(peers) - 1;
                 uint32_t before = 0;
                 if (lane == first) before = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
@@ -468,6 +453,32 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
                 } else {
                     if (is_live) s_stage[pos[j]] = k;
                 }
+            };
+#pragma unroll
+            for (int j = 0; j < ITEMS; j += 2) {
+                // Slot j by shared-memory peer masks; slot j+1 by ballots,
+                // computed while slot j's mask updates settle.
+                const bool live0 = FULL || j * 32 + lane < left;
+                const K k0 = read_key(keys[j * 32]);
+                const uint32_t d0 = digit_of(k0);
+                __syncwarp();
+                if (live0) atomicOr(&mask[d0], 1u << lane);
+                K k1 = 0;
+                uint32_t d1 = 0, peers1 = 0;
+                bool live1 = false;
+                if (j + 1 < ITEMS) {
+                    live1 = FULL || (j + 1) * 32 + lane < left;
+                    const uint32_t lv1 = FULL ? 0xffffffffu : prefix_lanes((j + 1) * 32, left);
+                    k1 = read_key(keys[(j + 1) * 32]);
+                    d1 = digit_of(k1);
+                    peers1 = match_label<RADIX_BITS>(d1) & lv1;
+                }
+                __syncwarp();
+                const uint32_t peers0 = live0 ? mask[d0] : 0u;
+                __syncwarp();
+                if (live0 && (peers0 & lt) == 0) mask[d0] = 0;
+                finish(j, k0, d0, peers0, live0);
+                if (j + 1 < ITEMS) finish(j + 1, k1, d1, peers1, live1);
             }
         };
         if (valid == TILE)
