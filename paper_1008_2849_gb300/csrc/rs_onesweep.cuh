@@ -442,14 +442,14 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
             constexpr bool FULL = decltype(full)::value;
             const uint32_t left = FULL ? WARP_ITEMS : (valid > wofs ? valid - wofs : 0u);
             const K* keys = in_k + wofs + lane;
-            auto finish = [&](int j, K k, uint32_t d, uint32_t peers, bool is_live) {
+            auto finish = [&](int j, K k, uint32_t d, uint32_t peers, bool is_live, uint32_t val) {
                 const uint32_t first = __ffs(peers) - 1;
                 uint32_t before = 0;
                 if (lane == first) before = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
                 before = __shfl_sync(0xffffffffu, before, first & 31u);
                 pos[j] = before + __popc(peers & lt);
                 if constexpr (PACKED) {
-                    if (is_live) s_stage2[pos[j]] = make_uint2((uint32_t)k, (uint32_t)in_v[wofs + j * 32 + lane]);
+                    if (is_live) s_stage2[pos[j]] = make_uint2((uint32_t)k, val);
                 } else {
                     if (is_live) s_stage[pos[j]] = k;
                 }
@@ -457,19 +457,23 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
 #pragma unroll
             for (int j = 0; j < ITEMS; j += 2) {
                 // Slot j by shared-memory peer masks; slot j+1 by ballots,
-                // computed while slot j's mask updates settle.
+                // computed while slot j's mask updates settle.  Both slots'
+                // keys (and values) are read first, so their loads overlap.
+                const bool two = j + 1 < ITEMS;
                 const bool live0 = FULL || j * 32 + lane < left;
                 const K k0 = read_key(keys[j * 32]);
+                const K k1 = two ? read_key(keys[(j + 1) * 32]) : K(0);
+                const V* const vals = in_v + wofs + lane;
+                const uint32_t v0 = PACKED ? (uint32_t)vals[j * 32] : 0u;
+                const uint32_t v1 = PACKED && two ? (uint32_t)vals[(j + 1) * 32] : 0u;
                 const uint32_t d0 = digit_of(k0);
                 __syncwarp();
                 if (live0) atomicOr(&mask[d0], 1u << lane);
-                K k1 = 0;
                 uint32_t d1 = 0, peers1 = 0;
                 bool live1 = false;
-                if (j + 1 < ITEMS) {
+                if (two) {
                     live1 = FULL || (j + 1) * 32 + lane < left;
                     const uint32_t lv1 = FULL ? 0xffffffffu : prefix_lanes((j + 1) * 32, left);
-                    k1 = read_key(keys[(j + 1) * 32]);
                     d1 = digit_of(k1);
                     peers1 = match_label<RADIX_BITS>(d1) & lv1;
                 }
@@ -477,8 +481,8 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
                 const uint32_t peers0 = live0 ? mask[d0] : 0u;
                 __syncwarp();
                 if (live0 && (peers0 & lt) == 0) mask[d0] = 0;
-                finish(j, k0, d0, peers0, live0);
-                if (j + 1 < ITEMS) finish(j + 1, k1, d1, peers1, live1);
+                finish(j, k0, d0, peers0, live0, v0);
+                if (two) finish(j + 1, k1, d1, peers1, live1, v1);
             }
         };
         if (valid == TILE)
