@@ -454,18 +454,21 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
                     if (is_live) s_stage[pos[j]] = k;
                 }
             };
+            const V* const vals = in_v + wofs + lane;
+            K nk0 = read_key(keys[0]);
+            K nk1 = ITEMS > 1 ? read_key(keys[32]) : K(0);
+            uint32_t nv0 = PACKED ? (uint32_t)vals[0] : 0u;
+            uint32_t nv1 = PACKED && ITEMS > 1 ? (uint32_t)vals[32] : 0u;
 #pragma unroll
             for (int j = 0; j < ITEMS; j += 2) {
                 // Slot j by shared-memory peer masks; slot j+1 by ballots,
                 // computed while slot j's mask updates settle.  Both slots'
-                // keys (and values) are read first, so their loads overlap.
+                // keys (and values) were read during the pair before, so the
+                // loads overlap the ranking.
                 const bool two = j + 1 < ITEMS;
                 const bool live0 = FULL || j * 32 + lane < left;
-                const K k0 = read_key(keys[j * 32]);
-                const K k1 = two ? read_key(keys[(j + 1) * 32]) : K(0);
-                const V* const vals = in_v + wofs + lane;
-                const uint32_t v0 = PACKED ? (uint32_t)vals[j * 32] : 0u;
-                const uint32_t v1 = PACKED && two ? (uint32_t)vals[(j + 1) * 32] : 0u;
+                const K k0 = nk0, k1 = nk1;
+                const uint32_t v0 = nv0, v1 = nv1;
                 const uint32_t d0 = digit_of(k0);
                 __syncwarp();
                 if (live0) atomicOr(&mask[d0], 1u << lane);
@@ -481,6 +484,12 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
                 const uint32_t peers0 = live0 ? mask[d0] : 0u;
                 __syncwarp();
                 if (live0 && (peers0 & lt) == 0) mask[d0] = 0;
+                if (j + 2 < ITEMS) {  // the next pair's loads overlap this pair's tail
+                    nk0 = read_key(keys[(j + 2) * 32]);
+                    nk1 = j + 3 < ITEMS ? read_key(keys[(j + 3) * 32]) : K(0);
+                    nv0 = PACKED ? (uint32_t)vals[(j + 2) * 32] : 0u;
+                    nv1 = PACKED && j + 3 < ITEMS ? (uint32_t)vals[(j + 3) * 32] : 0u;
+                }
                 finish(j, k0, d0, peers0, live0, v0);
                 if (two) finish(j + 1, k1, d1, peers1, live1, v1);
             }
