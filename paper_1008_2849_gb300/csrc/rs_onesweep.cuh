@@ -81,20 +81,21 @@ struct OnesweepSmem {
 //     every digit (warps before it come first).
 //  2. Ranking (per warp, item slot j at a time): the lanes holding the same
 //     digit come from one ballot per digit bit (odd slots) or from a shared
-//     peer mask each lane ORs its bit into (even slots) -- alternating keeps
-//     both the integer and the shared-memory pipes busy, and an odd slot's
-//     ballots run while the even slot before it waits for its mask; the lowest lane of the
-//     group adds the group's size to the warp's position counter of the digit;
-//     an item's tile position is the counter's old value plus the number of its
-//     peers on lower lanes.  The key is written straight to that position of
-//     the staging buffer.
+//     peer mask each lane ORs its bit into (even slots).  Alternating keeps
+//     both the integer and the shared-memory pipes busy; slots go in pairs,
+//     an odd slot's ballots running while the even slot before it waits for
+//     its mask.  The lowest lane of a group adds the group's size to the
+//     warp's position counter of the digit; an item's tile position is the
+//     counter's old value plus the number of its peers on lower lanes.  The
+//     key (with its value, for 32-bit pairs) is written straight to that
+//     position of the staging buffer.
 //  3. Look-back (threads b < 256): read the status words of the WINDOW tiles
 //     before this one at once, add AGG counts from the nearest one on until an
 //     INC prefix, re-reading from the first tile that has not published yet;
 //     publish this tile's inclusive prefix (INC).  Meanwhile the other warps
 //     count the next tile; its counts are published while this tile is
-//     stored.  A CTA takes
-//     its next tile id only after its look-back, so between taking an id and
+//     stored.  A CTA takes its next tile id only after its look-back (and
+//     starts pulling that tile into L2), so between taking an id and
 //     publishing that tile's counts it waits on no other CTA; every tile before
 //     this one has therefore published its counts or will without waiting, and
 //     the earliest unfinished tile always progresses.  Every wait is bounded by
@@ -105,9 +106,10 @@ struct OnesweepSmem {
 //  5. Slot s of the staging buffer is stored to
 //       dst[G[b] + prefix_before_this_tile[b] + (s - tile_excl[b])],
 //     so consecutive threads store consecutive addresses of one bucket run.
-//     Threads >= 256 start with a larger share of the slots while threads <
-//     256 prepare the next tile (its counts, AGG and warp bases).  Every
-//     global store is checked against n (ERR_BOUNDS instead of a fault).
+//     Threads >= 256 store most of the slots (all of them for 32-bit pairs)
+//     while threads < 256 prepare the next tile (its counts, AGG and warp
+//     bases).  Every global store is checked against n (ERR_BOUNDS instead
+//     of a fault).
 // ---------------------------------------------------------------------------
 // Typed keys (TYPED; 32-bit or 64-bit): the first pass that moves data maps
 // every key it reads onto its ordered unsigned word (key_to_ordered), so all
