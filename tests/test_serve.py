@@ -82,6 +82,31 @@ def test_every_result_is_its_own_sort_cpu():
         assert len({by_id[i].with_values for i in b}) == 1
 
 
+def test_completion_callback_sees_every_result_cpu():
+    """on_done receives every request once, with its result; the returned
+    list then keeps requests and latencies only (results are not retained)."""
+    reqs = _reqs(40, 5)
+    seen = {}
+
+    def on_done(d):
+        r = d.request
+        assert r.id not in seen
+        k = host_keys(r, POOL_N)
+        v = inputs.index_values(r.n) if r.with_values else None
+        ko, vo = oracle.sort_pairs(k, v)
+        assert np.array_equal(d.keys, ko)
+        if r.with_values:
+            assert np.array_equal(d.vals, vo)
+        seen[r.id] = d.batch
+
+    srv = SortServer(FakeExecutor(), budget_bytes=10**9, max_inflight=4, small_max=2000,
+                     batch_items=5000, keep_results=True, on_done=on_done)
+    res = srv.run(reqs, realtime=False)
+    assert sorted(seen) == sorted(r.id for r in reqs)
+    assert all(d.keys is None and d.vals is None for d in res["done"])
+    assert {d.request.id: d.batch for d in res["done"]} == seen
+
+
 def test_budget_is_never_exceeded_cpu():
     reqs = _reqs(80, 4, 2.0, 4.0)
     ex = FakeExecutor(delay=5)
