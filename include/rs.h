@@ -267,8 +267,11 @@ rs_status rs_graph_destroy(rs_graph graph);
  *  - Asynchronous: the caller collects device-side errors with
  *    rs_stream_status().
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    process; make that first call before any stream capture.  If the
+ *    lookup fails the call returns RS_ERR_CUDA and the next call tries
+ *    again.  cudaDeviceReset invalidates the kept address: do not call this
+ *    entry point on a device after resetting it.
  *  - Every call on a device shares the one array (each call clears what must
  *    start at zero), so calls whose work overlaps on the GPU -- two streams,
  *    or two host threads -- race and corrupt each other's results; order

@@ -36,7 +36,12 @@ extern "C" rs_status rs_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, s
             // The array's name is a host-side stand-in; its address on this
             // device (the current one) is looked up once and cached.
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return RS_ERR_CUDA;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+                // Clear the runtime's last error, so that a later, unrelated
+                // launch check does not report this failure as its own.
+                (void)cudaGetLastError();
+                return RS_ERR_CUDA;
+            }
             g_scratch_on[dev] = p;
         }
         scratch = g_scratch_on[dev];

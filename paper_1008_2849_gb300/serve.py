@@ -93,9 +93,15 @@ class GpuExecutor:
 
     # -- sizes ---------------------------------------------------------------
     def bytes_for(self, sizes: List[int], with_values: bool, segmented: bool) -> int:
+        """Device bytes that launch() allocates for this work: keys, values,
+        the segment table and the workspace, each rounded up to the 512-byte
+        blocks of PyTorch's caching allocator."""
+        def block(b):
+            return (int(b) + 511) // 512 * 512
         n = int(sum(sizes))
-        data = n * (8 if with_values else 4) + (4 * (len(sizes) + 1) if segmented else 0)
-        return data + int(self.rs.workspace_bytes(n, with_values, len(sizes) if segmented else 0))
+        ws = int(self.rs.workspace_bytes(n, with_values, len(sizes) if segmented else 0))
+        return (block(4 * n) + (block(4 * n) if with_values else 0)
+                + (block(4 * (len(sizes) + 1)) if segmented else 0) + block(max(ws, 1) + 256))
 
     # -- launches ------------------------------------------------------------
     def launch(self, reqs: List[Request], segmented: bool):
@@ -120,8 +126,8 @@ class GpuExecutor:
             ws = rs.alloc_workspace(n, pairs, len(reqs) if segmented else 0, device=self.device)
             table = None
             if segmented:
-                table = torch.tensor(np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64),
-                                     device=self.device).to(torch.int32)
+                host = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint32)
+                table = torch.from_numpy(host.view(np.int32)).to(self.device)
                 if pairs:
                     rs.sort_pairs_segmented_ex(keys, vals, table, ws, stream=s)
                 else:
@@ -172,13 +178,61 @@ class SortServer:
         self.keep = keep_results
         self.on_done = on_done
         self.peak_bytes = 0
+        self.launch_log: List[list] = []
+
+    def _fitting_prefix(self, batch: List[Request], with_values: bool, used: int):
+        """The longest prefix of `batch` whose segmented launch fits the
+        budget next to `used` bytes, and its bytes ([], 0 if none does)."""
+        def need(k):
+            return self.ex.bytes_for([r.n for r in batch[:k]], with_values, True)
+        lo, hi = 0, len(batch)  # prefix lengths: lo fits (or is empty), hi is the candidate
+        if used + need(hi) <= self.budget:
+            return batch, need(hi)
+        hi -= 1
+        while lo < hi:  # the bytes grow with the prefix: largest k that fits
+            mid = (lo + hi + 1) // 2
+            if used + need(mid) <= self.budget:
+                lo = mid
+            else:
+                hi = mid - 1
+        return (batch[:lo], need(lo)) if lo else ([], 0)
+
+    def _collect(self, inflight, done: List[Done], now, realtime: bool):
+        """Take every completed launch of `inflight`: its requests go to
+        `done` (and to on_done).  Returns the launches still running and the
+        bytes the completed ones held.  The completed handles are dropped
+        before this returns, so their device buffers are free by then."""
+        still, freed = [], 0
+        for entry in inflight:
+            h, rs_, b, li = entry
+            if not self.ex.poll(h):
+                still.append(entry)
+                continue
+            tdone = now()
+            self.launch_log[li][1] = tdone
+            for r, (k, v) in zip(rs_, self.ex.take(h, self.keep)):
+                d = Done(r, tdone - r.arrival if realtime else tdone, len(rs_), k, v)
+                if self.on_done is not None:
+                    self.on_done(d)
+                    d = Done(d.request, d.latency, d.batch)
+                done.append(d)
+            freed += b
+        return still, freed
 
     def run(self, requests: List[Request], realtime: bool = True) -> dict:
         """Serve `requests` (sorted by arrival).  With realtime, a request is
-        visible only once the wall clock passes its arrival time."""
+        visible only once the wall clock passes its arrival time.
+
+        The budget bounds the device bytes of the work in flight (its input
+        buffers, segment tables and workspaces) as the executor counts them.
+        Results handed out after completion (keep_results, on_done) are no
+        longer charged, and the executor's resident key pool is outside it."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         waiting = collections.deque()
-        inflight = []          # (handle, [requests], bytes)
+        inflight = []          # (handle, [requests], bytes, index in launch_log)
+        # Per launch: [time launched, time seen complete, requests]; seconds
+        # after the start of the run.
+        self.launch_log = []
         done: List[Done] = []
         used = 0
         nxt = 0
@@ -194,20 +248,8 @@ class SortServer:
                 waiting.append(reqs[nxt])
                 nxt += 1
             # Completions free memory and a slot.
-            still = []
-            for h, rs_, b in inflight:
-                if self.ex.poll(h):
-                    tdone = now()
-                    for r, (k, v) in zip(rs_, self.ex.take(h, self.keep)):
-                        d = Done(r, tdone - r.arrival if realtime else tdone, len(rs_), k, v)
-                        if self.on_done is not None:
-                            self.on_done(d)
-                            d = Done(d.request, d.latency, d.batch)
-                        done.append(d)
-                    used -= b
-                else:
-                    still.append((h, rs_, b))
-            inflight = still
+            inflight, freed = self._collect(inflight, done, now, realtime)
+            used -= freed
             # Admission, in arrival order.
             while waiting and len(inflight) < self.max_inflight:
                 head = waiting[0]
@@ -220,13 +262,17 @@ class SortServer:
                             break
                         batch.append(r)
                         total += r.n
-                    need = self.ex.bytes_for([r.n for r in batch], head.with_values, True)
-                    if used + need > self.budget:
+                    batch, need = self._fitting_prefix(batch, head.with_values, used)
+                    if not batch:
+                        if not inflight:
+                            raise MemoryError("request %d needs %d bytes, more than the budget"
+                                              % (head.id, self.ex.bytes_for(
+                                                  [head.n], head.with_values, True)))
                         break
                     for r in batch:
                         waiting.remove(r)
-                    h = self.ex.launch(batch, segmented=True)
-                    inflight.append((h, batch, need))
+                    inflight.append((self.ex.launch(batch, segmented=True), batch, need,
+                                     len(self.launch_log)))
                 else:
                     need = self.ex.bytes_for([head.n], head.with_values, False)
                     if used + need > self.budget:
@@ -235,8 +281,9 @@ class SortServer:
                                               % (head.id, need))
                         break
                     waiting.popleft()
-                    h = self.ex.launch([head], segmented=False)
-                    inflight.append((h, [head], need))
+                    inflight.append((self.ex.launch([head], segmented=False), [head], need,
+                                     len(self.launch_log)))
+                self.launch_log.append([now(), None, len(inflight[-1][1])])
                 used += need
                 launches += 1
                 self.peak_bytes = max(self.peak_bytes, used)
@@ -249,7 +296,8 @@ class SortServer:
         return {"done": sorted(done, key=lambda d: d.request.id), "wall_s": wall,
                 "items_per_s": items / wall, "p50_s": float(np.percentile(lat, 50)),
                 "p99_s": float(np.percentile(lat, 99)), "launches": launches,
-                "peak_bytes": self.peak_bytes, "budget_bytes": self.budget}
+                "peak_bytes": self.peak_bytes, "budget_bytes": self.budget,
+                "launch_log": self.launch_log}
 
 
 class SerialServer:

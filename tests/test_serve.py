@@ -124,6 +124,34 @@ def test_oversized_request_is_refused_cpu():
         srv.run(reqs, realtime=False)
 
 
+def test_oversized_small_request_is_refused_cpu():
+    """A small request that alone needs more than the budget, with nothing in
+    flight, raises instead of waiting forever."""
+    reqs = [Request(0, 50, True, "uniform", 1)]
+    srv = SortServer(FakeExecutor(), budget_bytes=1000, small_max=100)
+    with pytest.raises(MemoryError):
+        srv.run(reqs, realtime=False)
+
+
+def test_small_batch_shrinks_to_fit_budget_cpu():
+    """When a whole batch of small requests does not fit the budget, its
+    longest prefix that fits is launched, and the rest follow later."""
+    reqs = [Request(i, 1000, False, "uniform", i + 1) for i in range(6)]
+    ex = FakeExecutor(delay=2)
+    one = ex.bytes_for([1000], False, True)
+    budget = ex.bytes_for([1000, 1000], False, True) + one // 2  # two at once, not three
+    srv = SortServer(ex, budget_bytes=budget, max_inflight=8, small_max=2000,
+                     batch_items=10_000, keep_results=True)
+    res = srv.run(reqs, realtime=False)
+    assert len(res["done"]) == len(reqs)
+    assert res["peak_bytes"] <= budget
+    assert [len(b) for b in ex.launched][0] == 2
+    assert sorted(i for b in ex.launched for i in b) == list(range(6))
+    for d in res["done"]:
+        ko, _ = oracle.sort_pairs(host_keys(d.request, POOL_N), None)
+        assert np.array_equal(d.keys, ko)
+
+
 def test_admission_order_cpu():
     """Requests are admitted in arrival order (a large request at the head
     is not overtaken by later ones)."""
@@ -156,3 +184,80 @@ def test_gpu_results_alone_and_in_the_mix():
     # The serial baseline sorts the same requests one by one.
     ser = SerialServer(GpuExecutor(streams=1, pool_n=POOL_N)).run(reqs[:20], realtime=False)
     assert ser["items_per_s"] > 0
+
+
+def _host_results_and_peak(srv, reqs, realtime):
+    """Run `srv`, copying every result to the host as it completes (so no
+    device result outlives its launch); returns (results by id, run stats,
+    the allocator's peak bytes above its level at the start)."""
+    import torch
+    got = {}
+
+    def on_done(d):
+        k = d.keys.cpu().numpy().view(np.uint32).copy()
+        v = None if d.vals is None else d.vals.cpu().numpy().view(np.uint32).copy()
+        got[d.request.id] = (k, v)
+
+    srv.on_done = on_done
+    srv.keep = True
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    res = srv.run(reqs, realtime=realtime)
+    peak = torch.cuda.max_memory_allocated() - base
+    return got, res, peak
+
+
+def _check_against_oracle(reqs, got):
+    from tests.gpu_util import oracle_sort
+    for r in reqs:
+        k = host_keys(r, POOL_N)
+        v = inputs.index_values(r.n) if r.with_values else None
+        ko, vo = oracle_sort(k, v)
+        gk, gv = got[r.id]
+        assert np.array_equal(gk, ko), r.id
+        if r.with_values:
+            assert np.array_equal(gv, vo), r.id
+
+
+@pytest.mark.gpu
+def test_gpu_allocator_peak_within_budget():
+    """The device memory the allocator actually hands out while serving stays
+    within the server's budget, and the budget is what limits admission."""
+    from paper_1008_2849_gb300.serve import GpuExecutor
+    reqs = make_requests(150, 6, 3.0, 6.0)
+    ex = GpuExecutor(streams=3, pool_n=POOL_N)
+    largest = max(ex.bytes_for([r.n], r.with_values, False) for r in reqs)
+    budget = 3 * largest
+    srv = SortServer(ex, budget_bytes=budget, max_inflight=16, small_max=1 << 14,
+                     batch_items=1 << 17)
+    got, res, peak = _host_results_and_peak(srv, reqs, realtime=False)
+    assert len(res["done"]) == len(reqs)
+    assert res["peak_bytes"] <= budget
+    assert peak <= budget, (peak, budget)
+    # With at most 3 of the largest requests' bytes, the budget (not the
+    # 16 slots) bounds the launches in flight.
+    assert max(sum(1 for a, b, _ in res["launch_log"] if a <= t < b)
+               for t, _, _ in res["launch_log"]) < 16
+    _check_against_oracle(reqs, got)
+
+
+@pytest.mark.gpu
+def test_gpu_realtime_arrivals_overlap():
+    """Poisson arrivals in real time: requests are admitted while earlier
+    ones are still on the GPU (a launch starts before an earlier launch is
+    seen complete), and every result equals the oracle's sort of that
+    request alone."""
+    from paper_1008_2849_gb300.serve import GpuExecutor
+    reqs = make_requests(200, 7, 3.5, 6.5, rate_per_s=4000.0)
+    ex = GpuExecutor(streams=4, pool_n=POOL_N)
+    srv = SortServer(ex, budget_bytes=4 * 10**9, max_inflight=8, small_max=1 << 14,
+                     batch_items=1 << 17)
+    got, res, peak = _host_results_and_peak(srv, reqs, realtime=True)
+    assert len(res["done"]) == len(reqs)
+    log = res["launch_log"]
+    assert all(b is not None for _, b, _ in log)
+    overlapped = sum(1 for j in range(1, len(log)) if any(log[i][1] > log[j][0] for i in range(j)))
+    assert overlapped > 0, log[:10]
+    assert peak <= srv.budget
+    _check_against_oracle(reqs, got)
