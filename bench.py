@@ -8,6 +8,12 @@ passes) of 2^28 (uint32 key, uint32 value = index) pairs with uniform keys
 Every step sorts its own freshly copied input (2 GiB, far larger than the
 129 MB L2), so no step sees data left in cache by the previous one.
 
+On one GPU the line also carries the metric's other parts, from legs run
+after the timed region (bench_extras): the latency of a 2^20-key sort, the
+batched segmented sort of 4096 arrays (2^28 pairs) against a loop of
+per-array sorts, and the serving loop's p50/p99 latency against serial plain
+sorts, each with its own clock samples.
+
 Printed (rank 0, one JSON line): pairs/s for the whole job; the dominant
 kernel's achieved HBM bandwidth against the measured copy peak (roofline);
 the same metric end to end through rs_sort_pairs_host_batch with pinned host
@@ -170,9 +176,10 @@ def host_cpu_model() -> str:
         return "unknown"
 
 
-def cpu_oracle_rate(seconds_budget: float = 12.0, n_sample: int = 1 << 25):
-    """Time the CPU oracle (threaded, all host cores) on a bounded sample of
-    the workload: 2^25 uniform pairs (seed 2), value = index."""
+def cpu_oracle_rate(seconds_budget: float = 12.0, n_sample: int = N_PAIRS):
+    """Time the CPU oracle (threaded, all host cores) on the workload itself,
+    2^28 uniform pairs (seed 2), value = index: as many sorts as fit the
+    time budget, at most three."""
     import oracle
     oracle.build()
     threads = os.cpu_count() or 1
@@ -185,7 +192,7 @@ def cpu_oracle_rate(seconds_budget: float = 12.0, n_sample: int = 1 << 25):
         oracle.sort_pairs_threaded(k, v, threads)
         dt = time.perf_counter() - t0
         rates.append(n_sample / dt)
-        if time.perf_counter() - t_start > seconds_budget or len(rates) >= 5:
+        if time.perf_counter() - t_start > seconds_budget or len(rates) >= 3:
             break
     # The plain single-threaded oracle on a smaller bounded sample, for scale.
     n_one = 1 << 23
@@ -193,8 +200,9 @@ def cpu_oracle_rate(seconds_budget: float = 12.0, n_sample: int = 1 << 25):
     oracle.sort_pairs(k[:n_one], v[:n_one])
     single = n_one / (time.perf_counter() - t0)
     return {"value": statistics.median(rates), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d sorts of 2^25 uniform uint32 pairs (value = index), threaded LSD "
-                      "counting-sort oracle, median" % len(rates),
+            "sample": "%d sorts of the whole workload (2^%d uniform uint32 pairs, value = "
+                      "index), threaded LSD counting-sort oracle, median"
+                      % (len(rates), n_sample.bit_length() - 1),
             "single_thread_value": single,
             "single_thread_sample": "one sort of 2^23 of the same pairs, plain oracle, 1 thread",
             "cpu": host_cpu_model()}
@@ -222,7 +230,8 @@ def run_reference(args, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_PAIRS, "key_dist": "uniform", "seed": KEY_SEED,
-                   "values": "index", "reference_sample_n": n_sample},
+                   "values": "index", "reference_sample_n": n_sample,
+                   "same_config": n_sample == N_PAIRS},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "each step sorts 2^%d of the workload's pairs on the host "
                                    "(threaded LSD counting-sort oracle)" % args.reference_sample_log2,
@@ -241,7 +250,11 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--reference-sample-log2", type=int, default=24,
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the latency, batch and serving legs (run on one GPU only)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving stream in the serving leg")
+    ap.add_argument("--reference-sample-log2", type=int, default=28,
                     help="--impl reference: log2 of the pairs each step sorts on the host")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -384,6 +397,20 @@ def main():
                     "serial_bound": n / serial_s, "pipelined_bound": n / pipe_s,
                     "frac_of_pipelined_bound": (e2e["value"] / world) / (n / pipe_s)})
 
+    # The metric's other parts, on one GPU: the 2^20-key latency (config 1),
+    # the batched sort (config 4 rescaled to 2^28 pairs) and the serving
+    # loop's p50/p99 (a seeded prefix of the config-5 stream).
+    extras = {}
+    if world == 1 and not args.no_extras:
+        from paper_1008_2849_gb300 import bench_extras
+        torch.cuda.empty_cache()
+        extras["latency_2^20_keys"] = bench_extras.latency_keys_2pow20(local)
+        torch.cuda.empty_cache()
+        extras["batch"] = bench_extras.batch_2pow28(local)
+        torch.cuda.empty_cache()
+        extras["serve"] = bench_extras.serve_stream(local, requests=args.serve_requests)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate()
@@ -401,6 +428,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": launches,
+            "latency_2^20_keys_ms": (extras["latency_2^20_keys"]["call_ms"]
+                                     if "latency_2^20_keys" in extras else None),
+            **extras,
             "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"],
                        "reasons": cs["reasons"], "samples": cs["samples"], "source": cs["source"]},
         }
