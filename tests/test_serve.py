@@ -235,10 +235,19 @@ def test_gpu_allocator_peak_within_budget():
     assert len(res["done"]) == len(reqs)
     assert res["peak_bytes"] <= budget
     assert peak <= budget, (peak, budget)
-    # With at most 3 of the largest requests' bytes, the budget (not the
-    # 16 slots) bounds the launches in flight.
-    assert max(sum(1 for a, b, _ in res["launch_log"] if a <= t < b)
-               for t, _, _ in res["launch_log"]) < 16
+    _check_against_oracle(reqs, got)
+    # Requests of nearly equal size (each launched alone) under a budget of
+    # three of them: the budget, not the 16 slots, bounds the launches in
+    # flight, and the allocator stays within it.
+    reqs = make_requests(40, 8, 5.9, 6.0)
+    largest = max(ex.bytes_for([r.n], r.with_values, False) for r in reqs)
+    budget = 3 * largest
+    srv = SortServer(ex, budget_bytes=budget, max_inflight=16, small_max=1 << 14)
+    got, res, peak = _host_results_and_peak(srv, reqs, realtime=False)
+    log = res["launch_log"]
+    inflight = max(sum(1 for a, b, _ in log if a <= t < b) for t, _, _ in log)
+    assert 2 <= inflight <= 3, inflight
+    assert peak <= budget, (peak, budget)
     _check_against_oracle(reqs, got)
 
 
