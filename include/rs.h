@@ -316,18 +316,13 @@ typedef enum rs_tune_knob {
                                      take the one-warp shared-memory sort; 0 turns it off */
     RS_TUNE_SMALL_BITS = 7,       /* digit width of the one-warp and one-CTA sorts: 8 (four
                                      passes, the default) or 4 (eight passes) */
-    RS_TUNE_MSD = 8,              /* 1: unsigned whole arrays of up to 2^21 items may take the
+    RS_TUNE_MSD = 8               /* 1: unsigned whole arrays of up to 2^21 items may take the
                                      MSD-first order of Alg. 2 (one pass by the top digit, then
                                      every bucket sorted on chip) when no top-digit bucket holds
                                      more than 8192 keys; 0: always the four LSD passes */
-    RS_TUNE_PIPE = 9              /* 1: the scatter passes of unsigned 32-bit key-value whole
-                                     arrays below 2^30 items run the warp-specialised pipelined
-                                     kernel (one CTA per SM; teams that rank, count, look back
-                                     and store different tiles at once); 0: the tile shape of
-                                     RS_TUNE_TILE_PAIRS */
 } rs_tune_knob;
 
-/* Knobs 0, 1 and 4..9 are kept per size class of the item count -- the
+/* Knobs 0, 1 and 4..8 are kept per size class of the item count -- the
  * whole array's, or for a segmented sort the average segment's: class 0 up
  * to 2^13 items, 1 up to 2^16, 2 up to 2^20, 3 up to 2^24, 4 up to 2^28,
  * 5 above.  Knobs 2 and 3 are global. */

@@ -170,12 +170,11 @@ Knobs& knobs() {
     // 12); larger ones shape 3 (384 x 13, two CTAs per SM), and for keys only
     // shape 6 (384 x 18: no value buffer, still two CTAs).
     // Per class:
-    // {tile_pairs, tile_keys, tile_seg, small_max, warp_max, small_bits, msd,
-    //  pipe}.
+    // {tile_pairs, tile_keys, tile_seg, small_max, warp_max, small_bits, msd}.
     // The MSD-first order measured faster only up to 2^16 items (class 1).
-    static Knobs k{{{1, 1, 3, 8192, 512, 8, 0, 0}, {4, 1, 3, 4096, 512, 8, 1, 0},
-                    {1, 1, 3, 4096, 512, 8, 0, 0}, {3, 6, 3, 4096, 512, 8, 0, 1},
-                    {3, 6, 3, 4096, 512, 8, 0, 1}, {3, 6, 3, 4096, 512, 8, 0, 1}},
+    static Knobs k{{{1, 1, 3, 8192, 512, 8, 0}, {4, 1, 3, 4096, 512, 8, 1},
+                    {1, 1, 3, 4096, 512, 8, 0}, {3, 6, 3, 4096, 512, 8, 0},
+                    {3, 6, 3, 4096, 512, 8, 0}, {3, 6, 3, 4096, 512, 8, 0}},
                    kDefaultSpinLimit, 0, 4, 3};
     return k;
 }
@@ -728,10 +727,6 @@ static rs_status set_class_knob(ClassKnobs& c, int knob, int value) {
         if (value != 0 && value != 1) return RS_ERR_INVALID_ARG;
         c.msd = value;
         return RS_OK;
-    case 9:
-        if (value != 0 && value != 1) return RS_ERR_INVALID_ARG;
-        c.pipe = value;
-        return RS_OK;
     default: return RS_ERR_INVALID_ARG;
     }
 }
@@ -745,7 +740,6 @@ static int get_class_knob(const ClassKnobs& c, int knob) {
     case 6: return c.warp_max;
     case 7: return c.small_bits;
     case 8: return c.msd;
-    case 9: return c.pipe;
     default: return -1;
     }
 }

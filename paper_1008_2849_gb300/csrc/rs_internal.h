@@ -72,7 +72,6 @@ struct ClassKnobs {
     int warp_max;
     int small_bits;
     int msd;        // 1: whole arrays up to kMsdMaxItems may take the MSD-first order
-    int pipe;       // 1: unsigned 32-bit key-value scatter passes take k_onesweep_ws
 };
 // Largest whole array the MSD-first order is tried for: 256 buckets of at
 // most the one-CTA sort's capacity.
@@ -142,15 +141,6 @@ rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
 // the ordered words of typed keys, and clearing clear_bytes at `clear`.
 rs_status enqueue_hist4(const uint32_t* keys, uint32_t n, uint32_t* hist, void* clear,
                         size_t clear_bytes, uint32_t key_type, cudaStream_t stream);
-
-// Warp-specialised scatter pass of unsigned 32-bit keys with 32-bit values
-// (rs_pipeline.cu): whole arrays of fewer than 2^30 items (32-bit status
-// words); its tile (items) is pipeline_tile().
-rs_status launch_pipeline_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
-                                uint32_t n, uint32_t pass, uint32_t slot, Ctrl* ctrl,
-                                uint32_t* sticky, void* status, void* status_clear,
-                                cudaStream_t stream);
-uint32_t pipeline_tile();
 
 // Segmented scatter passes: per-tile geometry and per-segment bucket bases
 // built on the device, and an upper bound of the tile count for the launch.

@@ -144,9 +144,6 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
 
     const int cfg = pairs ? ck.tile_pairs : ck.tile_keys;
-    // Unsigned key-value arrays below 2^30 items may take the warp-specialised
-    // pass (its status words are 32-bit).
-    const bool pipe = pairs && ck.pipe != 0 && key_type == KEY_U32 && !L.wide_status;
     if (msd) {
         // One pass by digit 3 into the alternate buffers (skipped unless the
         // plan chose this order), then every bucket on chip back into the
@@ -169,9 +166,7 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     for (uint32_t p = 0; p < PASSES; ++p) {
         void* cur = status[p & 1];
         void* next = p + 1 < PASSES ? status[(p + 1) & 1] : nullptr;
-        st = pipe ? launch_pipeline_pairs(keys, vals, alt_k, alt_v, n, p, p, ctrl, di.sticky, cur,
-                                          next, stream)
-             : pairs ? launch_onesweep_pairs(cfg, L.wide_status, keys, vals, alt_k, alt_v, n, p, p,
+        st = pairs ? launch_onesweep_pairs(cfg, L.wide_status, keys, vals, alt_k, alt_v, n, p, p,
                                            ctrl, di.sticky, cur, next, nullptr, key_type, stream)
                    : launch_onesweep_keys(cfg, L.wide_status, keys, alt_k, n, p, p, ctrl, di.sticky,
                                           cur, next, nullptr, key_type, stream);
