@@ -22,9 +22,13 @@ neighbouring steps), next to one rs_sort_pairs_host call per array; the CPU
 oracle's throughput on a bounded sample (cpu_baseline); SM clocks sampled
 during the timed region.
 
-With N > 1 (torchrun), every rank sorts its own independent 2^28-pair array
-(replicas: the sort of one array does not shard without an exchange step),
-the time is the maximum over ranks, and the value counts all ranks' pairs.
+With N > 1 (torchrun) the ranks sort ONE array of N * 2^28 pairs held in
+shards, by Alg. 2's partition (--mode partition, the default there): every
+rank partitions its shard by the top byte, the bucket sizes are gathered,
+the items are exchanged by contiguous top-byte ranges balanced by count
+(NCCL all-to-all), and every rank sorts what it received.  --mode sort runs
+N independent replicas instead.  Either way the time is the maximum over
+ranks and the value counts all ranks' pairs.
 
 --impl reference times the CPU oracle (the plain LSD counting sort of the
 paper's Sec. 3/4, run on all host cores) on a bounded sample of the same
@@ -242,6 +246,113 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_partition(args, world, rank, local):
+    """One array of world * 2^28 pairs, rank r holding shard r (uniform keys,
+    seed per rank, value = global index), sorted across the ranks by Alg. 2's
+    partition (partition.py): local MSD pass, gather of bucket sizes,
+    exchange of the items by MSD range, local sort.  A step sorts the whole
+    array; value = all ranks' pairs per second over the max-over-ranks time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1008_2849_gb300 import build, clocks, partition, rs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    build.build_library()
+    rs.lib()
+    n = N_PAIRS
+    k_host = inputs.keys("uniform", n, seed=replica_seed(rank))
+    v_host = (np.arange(n, dtype=np.uint64) + np.uint64(rank) * np.uint64(n)).astype(np.uint32)
+    k_src = torch.from_numpy(k_host.view(np.int32)).to(dev)
+    v_src = torch.from_numpy(v_host.view(np.int32)).to(dev)
+    ops = partition.GpuOps(dev)
+    total = args.warmup + args.steps
+    bufs = [(k_src.clone(), v_src.clone()) for _ in range(total)]
+    stream = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        partition.partition_sort_pairs(bufs[i][0], bufs[i][1], ops)
+    rs.check_stream(stream)
+    received = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = rs.launch_count()
+    rs.profile_enable(True)
+    with clocks.ClockSampler(local) as sampler:
+        ev0.record(stream)
+        for i in range(args.warmup, total):
+            rk, _, bounds = partition.partition_sort_pairs(bufs[i][0], bufs[i][1], ops)
+            received.append(rk.numel())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    per_kind = rs.profile_read()
+    rs.profile_enable(False)
+    launches = rs.launch_count() - launches0
+    rs.check_stream(stream)
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    value = job_throughput(world, args.steps, n, elapsed_ms / 1e3)
+    # Scatter-pass roofline: every step runs one MSD pass over the shard and
+    # four passes over what the rank received.
+    peaks, peak_src = measured_peaks()
+    os_launches, os_ms = per_kind.get("onesweep", (0, 0.0))
+    items = args.steps * n + 4 * sum(received)
+    achieved = roofline.scatter_bytes_per_item(True) * items / (os_ms / 1e3) / 1e9 if os_ms else None
+    del bufs
+    torch.cuda.empty_cache()
+    # End to end: the shard uploaded from pinned host memory, sorted across
+    # the ranks, and this rank's part downloaded, every step.
+    kin = torch.from_numpy(k_host.view(np.int32)).pin_memory()
+    vin = torch.from_numpy(v_host.view(np.int32)).pin_memory()
+    e2e = None
+    if not args.no_e2e:
+        steps_e2e = max(3, min(args.steps, 5))
+        outs = []
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            kd, vd = kin.to(dev, non_blocking=True), vin.to(dev, non_blocking=True)
+            rk, rv, _ = partition.partition_sort_pairs(kd, vd, ops)
+            outs = (rk.cpu(), rv.cpu())
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_throughput(world, steps_e2e, n, dt), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * int(outs[0].numel()),
+               "api": "partition.partition_sort_pairs (pinned host shard in, this rank's part out)",
+               "steps": steps_e2e}
+    if rank == 0:
+        cs = sampler.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "sort_pairs_u32_%dx2^28_uniform_sharded" % world,
+                       "n": world * n, "shard": n, "key_dist": "uniform", "values": "global index",
+                       "passes": "1 MSD + 4 local", "digit_bits": 8,
+                       "l2": "inputs larger than L2: every step sorts its own fresh copy",
+                       "parallelism": "msd-partition (Alg. 2) over %d rank(s)" % world,
+                       "bucket_ranges": [int(x) for x in bounds]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s",
+                         "frac": achieved / float(peaks["hbm_gbs"]) if achieved else None,
+                         "traffic": None, "kernel": "k_onesweep (all scatter passes of a step)",
+                         "peak_source": peak_src + " (hbm_gbs, copy)"},
+            "e2e": e2e, "cpu_baseline": None, "gpu_launches": launches,
+            "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"],
+                       "reasons": cs["reasons"], "samples": cs["samples"], "source": cs["source"]},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,6 +365,10 @@ def main():
                     help="skip the latency, batch and serving legs (run on one GPU only)")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream in the serving leg")
+    ap.add_argument("--mode", choices=("auto", "sort", "partition"), default="auto",
+                    help="sort: every rank sorts its own array (replicas); partition: the ranks "
+                         "sort one array held in shards (Alg. 2); auto: sort on one GPU, "
+                         "partition on several")
     ap.add_argument("--reference-sample-log2", type=int, default=28,
                     help="--impl reference: log2 of the pairs each step sorts on the host")
     args = ap.parse_args()
@@ -263,6 +378,9 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    mode = args.mode if args.mode != "auto" else ("partition" if world > 1 else "sort")
+    if mode == "partition":
+        return run_partition(args, world, rank, local)
 
     import torch
     import torch.distributed as dist

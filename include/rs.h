@@ -192,6 +192,25 @@ rs_status rs_stream_status(void* cuda_stream);
 /* Static, human-readable name of a status code.  Never NULL. */
 const char* rs_status_string(rs_status status);
 
+/* Alg. 2's local step (Sec. 4, "reverse sorting"): one stable counting-sort
+ * pass by the most significant digit (bits 24..31) of n keys, with their
+ * values when d_vals != NULL, from (d_keys, d_vals) into (d_out_keys,
+ * d_out_vals), and the bucket offsets d_bucket_offsets[b] = the first output
+ * slot of digit value b (b = 0..255), d_bucket_offsets[256] = n.  Items of
+ * one bucket keep their input order.  This is the partition a rank performs
+ * before the exchange of the multi-GPU sort: each rank's output is grouped by
+ * bucket, so the items bound for a range of buckets are one contiguous slice.
+ *  - All pointers are device pointers; outputs must not overlap inputs;
+ *    d_out_vals is NULL exactly when d_vals is.  d_bucket_offsets holds 257
+ *    uint32_t and is overwritten.  The inputs are read, never written.
+ *  - Workspace: d_workspace of at least rs_workspace_bytes(n, d_vals != NULL,
+ *    0) bytes, 256-byte aligned.  Asynchronous on cuda_stream; allocates
+ *    nothing; device-side errors via rs_stream_status(). */
+rs_status rs_msd_partition_ex(const uint32_t* d_keys, const uint32_t* d_vals, size_t n,
+                              uint32_t* d_out_keys, uint32_t* d_out_vals,
+                              uint32_t* d_bucket_offsets, void* cuda_stream, void* d_workspace,
+                              size_t workspace_bytes);
+
 /* Digit histograms of n keys (counting step of Sec. 3 for all four digits at
  * once): d_hist[p*256 + b] = #{i : byte p of d_keys[i] == b}, p = 0..3,
  * b = 0..255.  d_hist is caller-owned device memory of 1024 uint32_t; it is

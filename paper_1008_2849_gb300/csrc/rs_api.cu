@@ -426,6 +426,40 @@ const char* rs_status_string(rs_status status) {
     }
 }
 
+rs_status rs_msd_partition_ex(const uint32_t* d_keys, const uint32_t* d_vals, size_t n,
+                               uint32_t* d_out_keys, uint32_t* d_out_vals,
+                               uint32_t* d_bucket_offsets, void* cuda_stream, void* d_workspace,
+                               size_t workspace_bytes) {
+    if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
+    if (d_bucket_offsets == nullptr || ((uintptr_t)d_bucket_offsets & 3u))
+        return RS_ERR_INVALID_ARG;
+    if ((d_vals == nullptr) != (d_out_vals == nullptr)) return RS_ERR_INVALID_ARG;
+    rs_status st = check_sort_args(d_keys, d_vals, n);
+    if (st != RS_OK) return st;
+    st = check_sort_args(d_out_keys, d_out_vals, n);
+    if (st != RS_OK) return st;
+    if (n > 0) {  // outputs apart from the inputs
+        auto apart = [n](const void* a, const void* b) {
+            const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b, len = n * sizeof(uint32_t);
+            return a == nullptr || b == nullptr || x + len <= y || y + len <= x;
+        };
+        if (!apart(d_keys, d_out_keys) || !apart(d_keys, d_out_vals) ||
+            !apart(d_vals, d_out_keys) || !apart(d_vals, d_out_vals))
+            return RS_ERR_INVALID_ARG;
+    }
+    const cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (n == 0) {
+        return cudaMemsetAsync(d_bucket_offsets, 0, 257 * sizeof(uint32_t), stream) ==
+                       cudaSuccess
+                   ? RS_OK
+                   : RS_ERR_CUDA;
+    }
+    if (d_workspace == nullptr || workspace_bytes < layout_for(n, d_vals != nullptr).total)
+        return RS_ERR_INVALID_ARG;
+    return enqueue_msd_partition(d_keys, d_vals, (uint32_t)n, d_out_keys, d_out_vals,
+                                 d_bucket_offsets, stream, d_workspace, workspace_bytes);
+}
+
 rs_status rs_digit_histograms_ex(const uint32_t* d_keys, size_t n, uint32_t* d_hist,
                                  void* cuda_stream) {
     if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;

@@ -259,6 +259,38 @@ k_plan(Ctrl* __restrict__ ctrl, uint32_t n, uint32_t msd_allowed, uint32_t warp_
 }
 
 // ---------------------------------------------------------------------------
+// k_msd_plan: the plan of one stable counting-sort pass by the most
+// significant digit (digit 3; Alg. 2's local MSD pass): G[3][b] = the
+// exclusive prefix of H[3], copied to bucket_off[0..255] with
+// bucket_off[256] = n, and the pass run (plan slot MSD_SLOT) from the input
+// to the output arrays even when every key has the same digit (then it is a
+// copy).  One CTA of 256 threads, thread b = bucket b.
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(RADIX)
+k_msd_plan(Ctrl* __restrict__ ctrl, uint32_t n, uint32_t* __restrict__ bucket_off) {
+    __shared__ uint32_t s_warp[RADIX / 32];
+    const uint32_t b = threadIdx.x, lane = b & 31, warp = b >> 5;
+    const uint32_t h = ctrl->hist[PASSES - 1][b];
+    uint32_t x = h;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t off = 0;
+    for (uint32_t w = 0; w < warp; ++w) off += s_warp[w];
+    const uint32_t first = off + x - h;
+    ctrl->gofs[PASSES - 1][b] = first;
+    bucket_off[b] = first;
+    if (b == 0) {
+        bucket_off[RADIX] = n;
+        ctrl->dir[MSD_SLOT] = DIR_A_TO_B;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_hist8: the eight digit histograms of 64-bit keys (K = 64, D = 8) in one
 // read of the keys, added into hist[p * 256 + b] (zeroed by the caller), via
 // a CTA-private shared histogram.  Typed keys (TYPED) are counted by the

@@ -115,6 +115,13 @@ Layout layout_for(size_t n, bool pairs);
 rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
                        void* workspace, size_t workspace_bytes, uint32_t key_type = 0);
 
+// Alg. 2's local MSD pass: one stable counting-sort pass of n (1 <= n <
+// 2^32) keys (with values when vals != nullptr) by digit 3 from the inputs
+// into the outputs, and the 257 bucket offsets; workspace as for a sort.
+rs_status enqueue_msd_partition(const uint32_t* keys, const uint32_t* vals, uint32_t n,
+                                uint32_t* out_keys, uint32_t* out_vals, uint32_t* bucket_off,
+                                cudaStream_t stream, void* workspace, size_t workspace_bytes);
+
 // Wide items: 64-bit keys (eight passes; key_type KEY_U64, KEY_I64 or
 // KEY_F64) carrying no, 32-bit or 64-bit values (val_bytes 0, 4 or 8), and
 // 32-bit keys (KEY_U32, KEY_I32, KEY_F32) carrying 64-bit values.  Every

@@ -101,6 +101,40 @@ rs_status enqueue_histograms(const uint32_t* keys, uint32_t n, uint32_t* hist,
     return enqueue_hist4(keys, n, hist, nullptr, 0, KEY_U32, stream);
 }
 
+rs_status enqueue_msd_partition(const uint32_t* keys, const uint32_t* vals, uint32_t n,
+                                uint32_t* out_keys, uint32_t* out_vals, uint32_t* bucket_off,
+                                cudaStream_t stream, void* workspace, size_t workspace_bytes) {
+    const bool pairs = vals != nullptr;
+    const Layout L = layout_for(n, pairs);
+    if (workspace == nullptr || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
+        return RS_ERR_INVALID_ARG;
+    DeviceInfo di;
+    rs_status st = device_info(&di);
+    if (st != RS_OK) return st;
+    char* ws = static_cast<char*>(workspace);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+    void* status = ws + L.status0;
+    const size_t status_bytes = L.status1 - L.status0;
+    if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream) != cudaSuccess) return RS_ERR_CUDA;
+    st = enqueue_hist4(keys, n, &ctrl->hist[0][0], status, status_bytes, KEY_U32, stream);
+    if (st != RS_OK) return st;
+    note_launch_begin(KK_PLAN, stream);
+    k_msd_plan<<<1, RADIX, 0, stream>>>(ctrl, n, bucket_off);
+    note_launch_end(KK_PLAN, stream);
+    if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
+    const ClassKnobs& ck = knobs().cls[size_class(n)];
+    // The scatter kernels read the source through the plan's direction
+    // (A -> B) and never write it.
+    uint32_t* src_k = const_cast<uint32_t*>(keys);
+    uint32_t* src_v = const_cast<uint32_t*>(vals);
+    return pairs ? launch_onesweep_pairs(ck.tile_pairs, L.wide_status, src_k, src_v, out_keys,
+                                         out_vals, n, PASSES - 1, MSD_SLOT, ctrl, di.sticky,
+                                         status, nullptr, nullptr, KEY_U32, stream)
+                 : launch_onesweep_keys(ck.tile_keys, L.wide_status, src_k, out_keys, n,
+                                        PASSES - 1, MSD_SLOT, ctrl, di.sticky, status, nullptr,
+                                        nullptr, KEY_U32, stream);
+}
+
 rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
                        void* workspace, size_t workspace_bytes, uint32_t key_type) {
     if (key_type > KEY_F32) return RS_ERR_INVALID_ARG;

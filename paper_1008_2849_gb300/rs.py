@@ -52,6 +52,7 @@ SIGNATURES = {
     "rs_stream_status": (_int, [_vp]),
     "rs_status_string": (ctypes.c_char_p, [_int]),
     "rs_digit_histograms_ex": (_int, [_vp, _sz, _vp, _vp]),
+    "rs_msd_partition_ex": (_int, [_vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz]),
     "rs_sort_pairs_host": (_int, [_vp, _vp, _vp, _vp, _sz]),
     "rs_sort_pairs_host_batch": (_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_uint32]),
     "rs_sort_pairs_noalloc": (_int, [_vp, _vp, _sz, _vp]),
@@ -314,6 +315,23 @@ def stream_status(stream=None) -> int:
 
 def check_stream(stream=None) -> None:
     _check(stream_status(stream), "rs_stream_status")
+
+
+def msd_partition_ex(keys, vals, out_keys, out_vals, bucket_offsets, workspace,
+                     stream=None) -> None:
+    """Enqueue Alg. 2's local MSD pass: (keys, vals) stably partitioned by
+    their top byte into (out_keys, out_vals); bucket_offsets (257 entries)
+    receives every bucket's first slot.  vals and out_vals may both be None."""
+    n = keys.numel()
+    if out_keys.numel() != n or (vals is not None and (vals.numel() != n or out_vals.numel() != n)):
+        raise ValueError("keys, values and outputs differ in length")
+    if bucket_offsets.numel() != 257:
+        raise ValueError("bucket_offsets must hold 257 entries")
+    _check(lib().rs_msd_partition_ex(
+        _dev_ptr(keys, "keys"), None if vals is None else _dev_ptr(vals, "vals"), n,
+        _dev_ptr(out_keys, "out_keys"), None if out_vals is None else _dev_ptr(out_vals, "out_vals"),
+        _dev_ptr(bucket_offsets, "bucket_offsets"), _stream_handle(stream), workspace.data_ptr(),
+        workspace.numel()), "rs_msd_partition_ex")
 
 
 def digit_histograms(keys, out=None, stream=None):
