@@ -182,6 +182,27 @@ rs_status rs_sort_kv_ex(void* d_keys, void* d_vals, size_t n, int key_type, int 
                         void* cuda_stream, void* d_workspace, size_t workspace_bytes);
 size_t rs_workspace_bytes_kv(size_t n, int key_type, int value_bits);
 
+/* The segmented form of rs_sort_kv_ex: items of every width, each segment
+ * [d_offsets[s], d_offsets[s+1]) sorted on its own (the plain definition of
+ * the sort applied per segment; the paper has no segmented case), for
+ * s = 0..num_segments-1.  The table follows the rules of
+ * rs_sort_pairs_segmented (nondecreasing, last entry <= n, each segment
+ * < 2^30 items; a bad table is reported as RS_ERR_BAD_SEGMENTS and nothing
+ * is written).  32-bit keys with no or 32-bit values take the 32-bit
+ * segmented sorts; every other combination sorts segments of up to 256
+ * items in one warp each (in shared memory) and every longer one with the
+ * scatter passes (eight for 64-bit keys).  Pointer, alignment, overlap and
+ * type rules as for rs_sort_kv_ex; workspace_bytes >=
+ * rs_workspace_bytes_kv_segmented(n, key_type, value_bits, num_segments),
+ * 256-byte aligned.  Asynchronous on cuda_stream, in place, stable;
+ * allocates nothing.  rs_workspace_bytes_kv_segmented returns 0 for n = 0,
+ * num_segments = 0 or unknown types. */
+rs_status rs_sort_kv_segmented_ex(void* d_keys, void* d_vals, size_t n, const uint32_t* d_offsets,
+                                  uint32_t num_segments, int key_type, int value_bits,
+                                  void* cuda_stream, void* d_workspace, size_t workspace_bytes);
+size_t rs_workspace_bytes_kv_segmented(size_t n, int key_type, int value_bits,
+                                       uint32_t num_segments);
+
 /* Synchronise cuda_stream (NULL = legacy default stream), then return and
  * clear the sticky device status word of the current device: RS_OK, or the
  * first device-side error recorded since the last call (RS_ERR_TIMEOUT,
@@ -335,16 +356,21 @@ typedef enum rs_tune_knob {
                                      take the one-warp shared-memory sort; 0 turns it off */
     RS_TUNE_SMALL_BITS = 7,       /* digit width of the one-warp and one-CTA sorts: 8 (four
                                      passes, the default) or 4 (eight passes) */
-    RS_TUNE_MSD = 8               /* 1: unsigned whole arrays of up to 2^21 items may take the
+    RS_TUNE_MSD = 8,              /* 1: unsigned whole arrays of up to 2^21 items may take the
                                      MSD-first order of Alg. 2 (one pass by the top digit, then
                                      every bucket sorted on chip) when no top-digit bucket holds
                                      more than 8192 keys; 0: always the four LSD passes */
+    RS_TUNE_TYPED_SPLIT = 9       /* signed and float keys: sorts of at least this many items
+                                     launch two instances of every scatter pass (the passes that
+                                     need no key map run without it, at the unsigned speed);
+                                     smaller sorts launch one instance per pass, which maps where
+                                     needed (half the launches) */
 } rs_tune_knob;
 
 /* Knobs 0, 1 and 4..8 are kept per size class of the item count -- the
  * whole array's, or for a segmented sort the average segment's: class 0 up
  * to 2^13 items, 1 up to 2^16, 2 up to 2^20, 3 up to 2^24, 4 up to 2^28,
- * 5 above.  Knobs 2 and 3 are global. */
+ * 5 above.  Knobs 2, 3 and 9 are global. */
 #define RS_NUM_SIZE_CLASSES 6
 
 /* Set a knob (a per-class knob in every class); RS_ERR_INVALID_ARG for an

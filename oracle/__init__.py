@@ -265,3 +265,23 @@ def sort_kv(keys, vals, key_type: str, lib=None):
     if rc:
         raise MemoryError("oracle_sort_kv failed (%d)" % rc)
     return ko, vo
+
+
+def sort_kv_segmented(keys, vals, offsets, key_type: str, lib=None):
+    """``sort_kv`` inside every segment [offsets[s], offsets[s+1]): the
+    definition of the segmented sort, one segment at a time; items outside
+    [offsets[0], offsets[-1]) are copied unchanged.  Returns new arrays."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    if offsets.size and (np.any(np.diff(offsets) < 0) or offsets[0] < 0
+                         or offsets[-1] > np.asarray(keys).size):
+        raise ValueError("malformed segment table")
+    ko = np.array(keys, copy=True)
+    vo = None if vals is None else np.array(vals, copy=True)
+    for a, b in zip(offsets[:-1], offsets[1:]):
+        if b - a < 2:
+            continue
+        sk, sv = sort_kv(ko[a:b], None if vo is None else vo[a:b], key_type, lib=lib)
+        ko[a:b] = sk
+        if vo is not None:
+            vo[a:b] = sv
+    return ko, vo

@@ -16,7 +16,9 @@
    (median step) and the number of scatter passes that ran -- a digit that is
    the same for every key makes its pass the identity, and it is skipped.
 3. Typed keys at 2^27 pairs of random 32-bit words (seed 21), read as
-   signed integers and as IEEE floats (rs_sort_typed_ex).
+   signed integers and as IEEE floats (rs_sort_typed_ex); and float-key
+   pairs of 2^14..2^26 items with two scatter-pass instances per pass
+   against one (RS_TUNE_TYPED_SPLIT), as graph replays.
 4. 64-bit keys with 32-bit values, 2^27 pairs of random words (seed 22),
    eight passes (rs_sort64_ex).
 5. Wide items through rs_sort_kv_ex at 2^27 items of random words (seed
@@ -174,6 +176,11 @@ def main(argv=None) -> int:
     out["pairs_2^27_typed_keys"] = typed
     del kb, vb, ws
 
+    # 3b. typed keys across sizes: two scatter-pass instances per pass (the
+    # middle passes without the key map) against one mapping instance per
+    # pass (half the launches), each as the replay of a captured graph.
+    out["typed_f32_pairs_split_vs_single"] = _typed_split_sweep(torch, rs, inputs, stream, a)
+
     # 4. 64-bit keys (eight passes) with 32-bit values, 2^27 pairs of random
     # words (seed 22): 1 GiB of keys.
     hi = inputs.splitmix32(22, n, 0).astype(np.uint64)
@@ -233,6 +240,39 @@ def main(argv=None) -> int:
     out["items_2^27_wide"] = wide
     print(json.dumps(out), flush=True)
     return 0
+
+
+def _typed_split_sweep(torch, rs, inputs, stream, a):
+    rows = {}
+    old = rs.tune_get("typed_split")
+    try:
+        for lg in (14, 16, 18, 20, 22, 24, 26):
+            n = 1 << lg
+            k = torch.from_numpy(inputs.keys("uniform", n, seed=24 + lg).view(np.int32)).cuda()
+            v = torch.arange(n, dtype=torch.int32, device="cuda")
+            kb, vb = torch.empty_like(k), torch.empty_like(v)
+            ws = rs.alloc_workspace(n, True)
+            row = {}
+            for name, split_min in (("two_instances", 0), ("one_instance", 0x7FFFFFFF)):
+                rs.tune_set("typed_split", split_min)
+                rs.sort_typed_ex(kb, vb, "f32", ws, stream)  # first use outside capture
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                side = torch.cuda.Stream()
+                with torch.cuda.graph(g, stream=side):
+                    rs.sort_typed_ex(kb, vb, "f32", ws, side)
+
+                def restore():
+                    kb.copy_(k)
+                    vb.copy_(v)
+                row[name + "_ms"] = _timed(torch, stream, g.replay, restore, a.steps, a.warmup)
+                del g
+            rs.check_stream()
+            rows["2^%d" % lg] = row
+            del k, v, kb, vb, ws
+    finally:
+        rs.tune_set("typed_split", old)
+    return rows
 
 
 def _executed_passes(hist, n):

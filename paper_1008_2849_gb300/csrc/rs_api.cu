@@ -19,6 +19,10 @@ namespace rs {
 namespace {
 
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
+// Typed sorts below this size launch one scatter-pass instance per pass
+// (measured on GB300, float-key pairs as graph replays: one instance is
+// 13 % faster at 2^14 items and 5 % at 2^24; two are 1.5 % faster at 2^26).
+constexpr uint32_t kDefaultTypedSplitMin = 1u << 25;
 constexpr int kMaxDevices = 64;
 // Device buffer sets of rs_sort_pairs_host_batch: with three, an array's
 // upload never waits for the download of the array two before it.
@@ -175,7 +179,7 @@ Knobs& knobs() {
     static Knobs k{{{1, 1, 3, 8192, 512, 8, 0}, {4, 1, 3, 4096, 512, 8, 1},
                     {1, 1, 3, 4096, 512, 8, 0}, {3, 6, 3, 4096, 512, 8, 0},
                     {3, 6, 3, 4096, 512, 8, 0}, {3, 6, 3, 4096, 512, 8, 0}},
-                   kDefaultSpinLimit, 0, 4, 3};
+                   kDefaultSpinLimit, 0, 4, 3, kDefaultTypedSplitMin};
     return k;
 }
 
@@ -406,6 +410,47 @@ rs_status rs_sort_kv_ex(void* d_keys, void* d_vals, size_t n, int key_type, int 
     return enqueue_sort_wide(d_keys, d_vals, (uint32_t)n, (uint32_t)key_type, (uint32_t)vb,
                              static_cast<cudaStream_t>(cuda_stream), d_workspace,
                              workspace_bytes);
+}
+
+size_t rs_workspace_bytes_kv_segmented(size_t n, int key_type, int value_bits,
+                                       uint32_t num_segments) {
+    if (n == 0 || num_segments == 0 || !valid_kv_types(key_type, value_bits)) return 0;
+    if (kv_is_narrow(key_type, value_bits))
+        return seg_layout_for(n, value_bits != 0, num_segments).total;
+    return seg_layout_wide(n, key_type >= RS_KEY_U64, (uint32_t)value_bits / 8, num_segments)
+        .total;
+}
+
+rs_status rs_sort_kv_segmented_ex(void* d_keys, void* d_vals, size_t n, const uint32_t* d_offsets,
+                                  uint32_t num_segments, int key_type, int value_bits,
+                                  void* cuda_stream, void* d_workspace, size_t workspace_bytes) {
+    if (!valid_kv_types(key_type, value_bits)) return RS_ERR_INVALID_ARG;
+    if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
+    if (kv_is_narrow(key_type, value_bits)) {
+        if ((value_bits == 0) != (d_vals == nullptr)) return RS_ERR_INVALID_ARG;
+        return ex_segmented(static_cast<uint32_t*>(d_keys), static_cast<uint32_t*>(d_vals), n,
+                            d_offsets, num_segments, cuda_stream, d_workspace, workspace_bytes,
+                            key_type);
+    }
+    const size_t kb = key_type >= RS_KEY_U64 ? 8 : 4, vb = (size_t)value_bits / 8;
+    if ((vb == 0) != (d_vals == nullptr)) return RS_ERR_INVALID_ARG;
+    if (n == 0 || num_segments == 0) return RS_OK;
+    if (d_keys == nullptr || d_offsets == nullptr || ((uintptr_t)d_offsets & 3u))
+        return RS_ERR_INVALID_ARG;
+    if (((uintptr_t)d_keys & (kb - 1)) || (vb && ((uintptr_t)d_vals & (vb - 1))))
+        return RS_ERR_INVALID_ARG;
+    if (vb) {
+        const uintptr_t k0 = (uintptr_t)d_keys, k1 = k0 + n * kb;
+        const uintptr_t v0 = (uintptr_t)d_vals, v1 = v0 + n * vb;
+        if (k0 < v1 && v0 < k1) return RS_ERR_INVALID_ARG;  // overlapping
+    }
+    if (d_workspace == nullptr ||
+        workspace_bytes < seg_layout_wide(n, kb == 8, (uint32_t)vb, num_segments).total)
+        return RS_ERR_INVALID_ARG;
+    return enqueue_sort_segmented_wide(d_keys, d_vals, (uint32_t)n, d_offsets, num_segments,
+                                       (uint32_t)key_type, (uint32_t)vb,
+                                       static_cast<cudaStream_t>(cuda_stream), d_workspace,
+                                       workspace_bytes);
 }
 
 rs_status rs_stream_status(void* cuda_stream) {
@@ -789,6 +834,10 @@ rs_status rs_tune_set(int knob, int value) {
         if (value < 0 || value > 3) return RS_ERR_INVALID_ARG;
         k.hist_mode = value;
         return RS_OK;
+    case 9:
+        if (value < 0) return RS_ERR_INVALID_ARG;
+        k.typed_split_min = (uint32_t)value;
+        return RS_OK;
     default:
         for (int c = 0; c < NUM_SIZE_CLASSES; ++c) {
             rs_status st = set_class_knob(k.cls[c], knob, value);
@@ -803,6 +852,7 @@ int rs_tune_get(int knob) {
     switch (knob) {
     case 2: return k.hist_ctas_per_sm;
     case 3: return k.hist_mode;
+    case 9: return (int)(k.typed_split_min > 0x7fffffffu ? 0x7fffffffu : k.typed_split_min);
     default: return get_class_knob(k.cls[4], knob);
     }
 }

@@ -88,7 +88,15 @@ struct Knobs {
     uint32_t debug;          // DBG_* bits
     int hist_ctas_per_sm;
     int hist_mode;           // HIST_ATOMIC / HIST_LEADER / HIST_MATCH
+    // Typed keys: sorts of at least this many items launch two instances of
+    // every scatter pass (the passes that need no key map run without it);
+    // smaller ones launch only the mapping instance, which runs every pass.
+    uint32_t typed_split_min;
 };
+Knobs& knobs();
+// Whether a typed sort of n items launches two instances of every scatter
+// pass (see Knobs::typed_split_min).
+inline bool typed_split(size_t n) { return n >= knobs().typed_split_min; }
 Knobs& knobs();
 
 // Host-side checks shared by the sort entry points: size, null pointers,
@@ -198,6 +206,13 @@ struct SegLayout {
     uint32_t max_tiles, max_large;
 };
 SegLayout seg_layout_for(size_t n, bool pairs, uint32_t num_segments);
+// Segmented sorts of wide items (64-bit keys, or 32-bit keys with 64-bit
+// values; rs_segmented_wide.cu).
+SegLayout seg_layout_wide(size_t n, bool key64, uint32_t val_bytes, uint32_t num_segments);
+rs_status enqueue_sort_segmented_wide(void* keys, void* vals, uint32_t n,
+                                      const uint32_t* offsets, uint32_t num_segments,
+                                      uint32_t key_type, uint32_t val_bytes, cudaStream_t stream,
+                                      void* workspace, size_t workspace_bytes);
 rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
                                  const uint32_t* offsets, uint32_t num_segments,
                                  cudaStream_t stream, void* workspace, size_t workspace_bytes,

@@ -119,7 +119,8 @@ struct OnesweepSmem {
 //
 // Segmented sorts (SEG): tiles never straddle a segment.  tile_geo[t] =
 // (first item, item count, first tile of its segment, segment) for every tile
-// of the large segments; seg_gofs[s][pass][b] is the absolute first output
+// of the large segments; seg_gofs[s][pass][b] (pass < 4, or < 8 for 64-bit
+// keys) is the absolute first output
 // slot of bucket b of segment s; the number of tiles is ctrl->seg_tiles.
 template <int THREADS, int ITEMS, int MIN_BLOCKS, bool PAIRS, typename S, int WINDOW, bool SEG,
           bool TYPED, typename K = uint32_t, typename V = uint32_t>
@@ -422,7 +423,7 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
         if (PACKED) wait_bar(2);  // this tile's values, read while ranking
         // Segmented: this tile's bucket bases, fetched now, used after ranking.
         uint32_t seg_base = 0;
-        if (SEG && tid < RADIX) seg_base = seg_gofs[((size_t)geo.w * PASSES + pass) * RADIX + tid];
+        if (SEG && tid < RADIX) seg_base = seg_gofs[((size_t)geo.w * NPASS + pass) * RADIX + tid];
         if (tid == ISSUER) s_err_seen = ld_relaxed(&ctrl->err);
         if (status_clear != nullptr)
             for (uint32_t b = tid; b < RADIX; b += THREADS)

@@ -65,9 +65,15 @@ static rs_status launch_onesweep_variant(int cfg, uint32_t* ka, uint32_t* va, ui
                                          const SegView& seg, uint32_t key_type,
                                          cudaStream_t stream) {
     if (key_type != KEY_U32) {
-        // Typed keys: the passes that need no maps run without them (see
-        // ROLE_PLAIN_PASSES); both instances are launched for every pass.
+        // Typed keys: from typed_split_min items on, the passes that need no
+        // maps run without them (see ROLE_PLAIN_PASSES) and both instances
+        // are launched for every pass; below it the mapping instance alone
+        // runs every pass, mapping where the plan needs it.
         using T = TileShape<kTypedShape>;
+        if (!typed_split(n))
+            return launch_onesweep_shape<T::threads, T::items, T::min_blocks, T::window, PAIRS, S,
+                                         SEG, true>(ka, va, kb, vb, n, pass, slot, ctrl, sticky,
+                                                    status, status_clear, seg, key_type, stream);
         const rs_status st =
             launch_onesweep_shape<T::threads, T::items, T::min_blocks, T::window, PAIRS, S, SEG,
                                   false>(ka, va, kb, vb, n, pass, slot, ctrl, sticky, status,

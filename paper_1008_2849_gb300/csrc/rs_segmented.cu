@@ -109,7 +109,7 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
     }
     note_launch_end(KK_SEG_HIST, stream);
     note_launch_begin(KK_SEG_SCAN, stream);
-    k_seg_scan<<<di.sm_count * 2, 1024, 0, stream>>>(ctrl, gofs, large_first);
+    k_seg_scan<PASSES><<<di.sm_count * 2, 1024, 0, stream>>>(ctrl, gofs, large_first);
     note_launch_end(KK_SEG_SCAN, stream);
     if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
 

@@ -29,14 +29,16 @@ namespace rs {
 //    segment, ordinal of its segment).
 //  - Tiny segments are listed in tiny_list, small ones in small_list (order
 //    irrelevant).
-//  - The pass plan runs all four passes (caller -> alternate -> ... -> caller).
+//  - The pass plan runs all npass passes (four, or eight for 64-bit keys;
+//    caller -> alternate -> ... -> caller).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
+static __global__ void __launch_bounds__(1024)
 k_seg_plan(const uint32_t* __restrict__ off, uint32_t num_segments, uint32_t n, uint32_t tile,
            uint32_t warp_max, uint32_t small_max, Ctrl* __restrict__ ctrl,
            uint32_t* __restrict__ sticky, uint4* __restrict__ tile_geo,
            uint32_t* __restrict__ tiny_list, uint32_t* __restrict__ small_list,
-           uint32_t* __restrict__ large_first /* [S] first item of large ordinal */) {
+           uint32_t* __restrict__ large_first /* [S] first item of large ordinal */,
+           uint32_t npass = PASSES) {
     __shared__ uint32_t s_carry[2];  // tiles and large segments before this chunk
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -53,7 +55,7 @@ k_seg_plan(const uint32_t* __restrict__ off, uint32_t num_segments, uint32_t n, 
     if (tid == 0) {
         s_carry[0] = 0;
         s_carry[1] = 0;
-        for (uint32_t p = 0; p < PASSES; ++p) ctrl->dir[p] = (p & 1) ? DIR_B_TO_A : DIR_A_TO_B;
+        for (uint32_t p = 0; p < npass; ++p) ctrl->dir[p] = (p & 1) ? DIR_B_TO_A : DIR_A_TO_B;
     }
     __syncthreads();
     for (uint32_t c = 0; c < num_segments; c += 1024) {
@@ -215,19 +217,23 @@ k_seg_hist(const uint32_t* __restrict__ keys, const Ctrl* __restrict__ ctrl,
 
 // ---------------------------------------------------------------------------
 // k_seg_scan: per large segment (one CTA of 1024 threads = 4 digits x 256
-// buckets), the exclusive prefix over buckets plus the segment's first item:
-// the absolute first output slot of every bucket, written over the histogram.
+// buckets, twice for the eight digits of 64-bit keys), the exclusive prefix
+// over buckets plus the segment's first item: the absolute first output slot
+// of every bucket, written over the histogram hist[segment][NP][256].
 // ---------------------------------------------------------------------------
+template <int NP = PASSES>
 __global__ void __launch_bounds__(1024)
 k_seg_scan(const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ hist,
            const uint32_t* __restrict__ large_first) {
+    static_assert(NP == 4 || NP == 8, "32-bit or 64-bit keys");
     __shared__ uint32_t s_warp[32];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = tid >> 8;
     if (ctrl->err != 0) return;
     const uint32_t large = ctrl->large_count;
-    for (uint32_t g = blockIdx.x; g < large; g += gridDim.x) {
-        uint32_t* h = hist + (size_t)g * PASSES * RADIX;
+    for (uint32_t g = blockIdx.x; g < large; g += gridDim.x)
+    for (uint32_t round = 0; round < NP / 4; ++round) {
+        uint32_t* h = hist + ((size_t)g * NP + 4 * round) * RADIX;
         const uint32_t v = h[tid];
         uint32_t x = v;
 #pragma unroll

@@ -31,8 +31,12 @@ rs_status pass64_typed(unsigned long long* ka, V* va, unsigned long long* kb, V*
     if (key_type == KEY_U64)
         return pass64<PAIRS, V, S, false>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
                                           status_clear, KEY_U32, stream);
-    // Typed keys: the passes that need no maps run without them (see
-    // ROLE_PLAIN_PASSES); both instances are launched for every pass.
+    // Typed keys: from typed_split_min items on, the passes that need no
+    // maps run without them (see ROLE_PLAIN_PASSES) and both instances are
+    // launched for every pass; below it the mapping instance runs them all.
+    if (!typed_split(n))
+        return pass64<PAIRS, V, S, true>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
+                                         status_clear, key_type, stream);
     const rs_status st = pass64<PAIRS, V, S, false>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
                                                     status_clear, key_type | ROLE_PLAIN_PASSES,
                                                     stream);

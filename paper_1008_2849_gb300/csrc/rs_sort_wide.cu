@@ -39,8 +39,14 @@ rs_status launch_pass_k32v64(uint32_t key_type, bool wide, uint32_t* ka, unsigne
                                                            status, status_clear, KEY_U32, stream)
                     : pass32v64<uint32_t, false>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
                                                  status_clear, KEY_U32, stream);
-    // Typed keys: the passes that need no maps run without them (see
-    // ROLE_PLAIN_PASSES); both instances are launched for every pass.
+    // Typed keys: from typed_split_min items on, the passes that need no
+    // maps run without them (see ROLE_PLAIN_PASSES) and both instances are
+    // launched for every pass; below it the mapping instance runs them all.
+    if (!typed_split(n))
+        return wide ? pass32v64<unsigned long long, true>(ka, va, kb, vb, n, pass, ctrl, sticky,
+                                                          status, status_clear, key_type, stream)
+                    : pass32v64<uint32_t, true>(ka, va, kb, vb, n, pass, ctrl, sticky, status,
+                                                status_clear, key_type, stream);
     const uint32_t plain = key_type | ROLE_PLAIN_PASSES, maps = key_type | ROLE_MAP_PASSES;
     rs_status st = wide ? pass32v64<unsigned long long, false>(ka, va, kb, vb, n, pass, ctrl, sticky,
                                                                status, status_clear, plain, stream)

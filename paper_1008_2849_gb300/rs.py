@@ -49,6 +49,8 @@ SIGNATURES = {
     "rs_workspace_bytes64": (_sz, [_sz, _int]),
     "rs_sort_kv_ex": (_int, [_vp, _vp, _sz, _int, _int, _vp, _vp, _sz]),
     "rs_workspace_bytes_kv": (_sz, [_sz, _int, _int]),
+    "rs_sort_kv_segmented_ex": (_int, [_vp, _vp, _sz, _vp, _u32, _int, _int, _vp, _vp, _sz]),
+    "rs_workspace_bytes_kv_segmented": (_sz, [_sz, _int, _int, _u32]),
     "rs_stream_status": (_int, [_vp]),
     "rs_status_string": (ctypes.c_char_p, [_int]),
     "rs_digit_histograms_ex": (_int, [_vp, _sz, _vp, _vp]),
@@ -260,6 +262,43 @@ def sort_kv(keys, vals=None, key_type: str = "u64", stream=None) -> None:
     check_stream(stream)
 
 
+def workspace_bytes_kv_segmented(n: int, key_type: str, value_bits: int, num_segments: int) -> int:
+    return int(lib().rs_workspace_bytes_kv_segmented(int(n), KV_KEY_TYPES[key_type][0],
+                                                     int(value_bits), int(num_segments)))
+
+
+def sort_kv_segmented_ex(keys, vals, offsets, key_type: str, workspace, stream=None) -> None:
+    """Enqueue the stable sort of every segment [offsets[s], offsets[s+1]) of
+    keys read as ``key_type`` (int32 or int64 tensors of bit patterns),
+    carrying int32 or int64 values, or None; offsets is an int32 tensor of
+    num_segments + 1 entries."""
+    code, kw = KV_KEY_TYPES[key_type]
+    value_bits = 0
+    vp = None
+    if vals is not None:
+        if vals.numel() != keys.numel():
+            raise ValueError("keys and vals differ in length")
+        value_bits = 8 * vals.element_size()
+        vp = _dev_ptr(vals, "vals", vals.element_size())
+    op, ns = _segments(offsets)
+    _check(lib().rs_sort_kv_segmented_ex(_dev_ptr(keys, "keys", kw), vp, keys.numel(), op, ns,
+                                         code, value_bits, _stream_handle(stream),
+                                         workspace.data_ptr(), workspace.numel()),
+           "rs_sort_kv_segmented_ex")
+
+
+def sort_kv_segmented(keys, vals, offsets, key_type: str = "u64", stream=None) -> None:
+    """Synchronous ``sort_kv_segmented_ex`` with a workspace allocated for the call."""
+    import torch
+    value_bits = 0 if vals is None else 8 * vals.element_size()
+    nbytes = max(workspace_bytes_kv_segmented(keys.numel(), key_type, value_bits,
+                                              offsets.numel() - 1), 1)
+    raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=keys.device)
+    pad = (-raw.data_ptr()) % 256
+    sort_kv_segmented_ex(keys, vals, offsets, key_type, raw[pad:pad + nbytes], stream)
+    check_stream(stream)
+
+
 def sort64(keys, vals=None, stream=None) -> None:
     """Synchronous 64-bit key sort with a workspace allocated for the call."""
     import torch
@@ -422,7 +461,8 @@ def profile_read() -> dict:
 
 
 TUNE_KNOBS = {"tile_pairs": 0, "tile_keys": 1, "hist_ctas_per_sm": 2, "hist_mode": 3,
-              "small_max": 4, "tile_seg": 5, "warp_max": 6, "small_bits": 7, "msd": 8}
+              "small_max": 4, "tile_seg": 5, "warp_max": 6, "small_bits": 7, "msd": 8,
+              "typed_split": 9}
 
 
 def tune_set(knob: str, value: int) -> None:

@@ -455,7 +455,26 @@ def pin_kv_radix_oracles(lib=None):
     assert np.array_equal(wide, _values64(n)[rv])
 
 
-KV_PINS = (pin_kv_numpy, pin_kv_double_total_order, pin_kv_bruteforce, pin_kv_radix_oracles)
+def pin_kv_segmented(lib=None):
+    """Segmented sort of every key type with 64-bit values: numpy's stable
+    argsort of the typed view inside each segment (empty and one-item
+    segments included); items outside the table's range are unchanged."""
+    sizes = [0, 1, 700, 2, 1500, 0, 797, 3]
+    off = inputs.offsets_from_sizes(sizes)
+    n = int(off[-1]) + 5  # five items past the last segment
+    for i, kt in enumerate(_NUMPY_VIEW):
+        k = _kv_keys(kt, n, seed=90 + i)
+        v = _values64(n)
+        ko, vo = oracle.sort_kv_segmented(k, v, off, kt, lib=lib)
+        for a, b in zip(off[:-1], off[1:]):
+            order = np.argsort(k[a:b].view(_NUMPY_VIEW[kt]), kind="stable")
+            assert np.array_equal(ko[a:b], k[a:b][order])
+            assert np.array_equal(vo[a:b], v[a:b][order])
+        assert np.array_equal(ko[off[-1]:], k[off[-1]:]) and np.array_equal(vo[off[-1]:], v[off[-1]:])
+
+
+KV_PINS = (pin_kv_numpy, pin_kv_double_total_order, pin_kv_bruteforce, pin_kv_radix_oracles,
+           pin_kv_segmented)
 
 TYPED_PINS = (pin_typed_i32_numpy, pin_typed_f32_numpy, pin_typed_f32_total_order,
               pin_typed_stability, pin_typed_segmented)

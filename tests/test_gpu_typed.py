@@ -122,3 +122,25 @@ def test_unknown_key_type_is_rejected(rs):
     code = rs.lib().rs_sort_typed_ex(ctypes.c_void_p(k.data_ptr()), None, 100, 3, None,
                                      ctypes.c_void_p(ws.data_ptr()), ws.numel())
     assert code == 1
+
+
+@pytest.mark.parametrize("kind,key_type,n", [("words", "f32", 300_007), ("narrow", "f32", 70_001),
+                                             ("small_ints", "i32", 1_000_003),
+                                             ("words", "i32", 9000)])
+def test_typed_one_or_two_instances(rs, kind, key_type, n):
+    """Typed sorts with two scatter-pass instances per pass (the middle
+    passes without the key map) and with one mapping instance per pass give
+    the oracle's result either way, skipped passes included."""
+    k = _keys(kind, n, seed=130)
+    v = inputs.index_values(n)
+    ko, vo = oracle.sort_typed(k, v, key_type)
+    old = rs.tune_get("typed_split")
+    try:
+        for split_min in (0, 0x7FFFFFFF):
+            rs.tune_set("typed_split", split_min)
+            kd, vd = to_dev(k), to_dev(v)
+            rs.sort_typed(kd, vd, key_type)
+            assert np.array_equal(to_host(kd), ko), split_min
+            assert np.array_equal(to_host(vd), vo), split_min
+    finally:
+        rs.tune_set("typed_split", old)

@@ -236,10 +236,11 @@ def test_gpu_allocator_peak_within_budget():
     assert res["peak_bytes"] <= budget
     assert peak <= budget, (peak, budget)
     _check_against_oracle(reqs, got)
-    # Requests of nearly equal size (each launched alone) under a budget of
-    # three of them: the budget, not the 16 slots, bounds the launches in
-    # flight, and the allocator stays within it.
-    reqs = make_requests(40, 8, 5.9, 6.0)
+    # Key-value requests of nearly equal size (each launched alone) under a
+    # budget of three of them: the budget, not the 16 slots, bounds the
+    # launches in flight, and the allocator stays within it.
+    sizes = 900_000 + (inputs.splitmix32(8, 40, 0) % np.uint32(100_000)).astype(np.int64)
+    reqs = [Request(i, int(m), True, "uniform", 100 + i) for i, m in enumerate(sizes)]
     largest = max(ex.bytes_for([r.n], r.with_values, False) for r in reqs)
     budget = 3 * largest
     srv = SortServer(ex, budget_bytes=budget, max_inflight=16, small_max=1 << 14)
@@ -258,7 +259,7 @@ def test_gpu_realtime_arrivals_overlap():
     seen complete), and every result equals the oracle's sort of that
     request alone."""
     from paper_1008_2849_gb300.serve import GpuExecutor
-    reqs = make_requests(200, 7, 3.5, 6.5, rate_per_s=4000.0)
+    reqs = make_requests(200, 7, 3.5, 6.0, rate_per_s=4000.0)
     ex = GpuExecutor(streams=4, pool_n=POOL_N)
     srv = SortServer(ex, budget_bytes=4 * 10**9, max_inflight=8, small_max=1 << 14,
                      batch_items=1 << 17)
