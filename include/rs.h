@@ -82,6 +82,23 @@ rs_status rs_sort_keys_ex(uint32_t* d_keys, size_t n,
 rs_status rs_sort_pairs_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n,
                            void* cuda_stream, void* d_workspace, size_t workspace_bytes);
 
+/* The same sort with wider digits: three stable counting-sort passes of
+ * 11, 11 and 10 bits (Sec. 4 with D = 11, so ceil(32 / D) = 3 passes instead
+ * of four), keys only (d_vals == NULL) or pairs.  The result is the same as
+ * rs_sort_pairs_ex / rs_sort_keys_ex: ascending, stable, in place.
+ * Every pass is a reduce-then-scan over 2048 buckets: per-chunk digit counts,
+ * their prefix over chunks, then a tile-by-tile scatter of every chunk.
+ * Arguments as rs_sort_pairs_ex; workspace (256-byte aligned) of at least
+ * rs_workspace_bytes_digits11(n, d_vals != NULL) bytes -- two alternate
+ * buffers, since an odd pass count ends in the caller's arrays only by
+ * rotating through three.  Asynchronous; a bounds-check failure inside a
+ * kernel is reported by rs_stream_status as RS_ERR_BOUNDS. */
+rs_status rs_sort_digits11_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n, void* cuda_stream,
+                              void* d_workspace, size_t workspace_bytes);
+/* Workspace bytes of rs_sort_digits11_ex; 0 for n == 0 or n >= 2^32.  Pure
+ * host arithmetic. */
+size_t rs_workspace_bytes_digits11(size_t n, int with_values);
+
 /* Segmented sorts: every segment [d_offsets[s], d_offsets[s+1]) of the n-item
  * array, s = 0..num_segments-1, is sorted on its own, stably and ascending,
  * exactly as if it were a separate array (the paper has no segmented case;

@@ -203,6 +203,9 @@ const char* kernel_kind_name(int kind) {
     case KK_SEG_SCAN: return "seg_scan";
     case KK_SEG_ONESWEEP: return "seg_onesweep";
     case KK_WARP: return "warp_sort";
+    case KK_D11_UP: return "d11_up";
+    case KK_D11_SCAN: return "d11_scan";
+    case KK_D11_DOWN: return "d11_down";
     default: return nullptr;
     }
 }
@@ -264,6 +267,21 @@ rs_status rs_sort_pairs_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n, void* c
                            void* d_workspace, size_t workspace_bytes) {
     if (n > 0 && d_vals == nullptr) return RS_ERR_INVALID_ARG;
     return ex_sort(d_keys, d_vals, n, cuda_stream, d_workspace, workspace_bytes);
+}
+
+size_t rs_workspace_bytes_digits11(size_t n, int with_values) {
+    if (n == 0 || n >= (size_t(1) << 32)) return 0;
+    return layout11(n, with_values != 0).total;
+}
+
+rs_status rs_sort_digits11_ex(uint32_t* d_keys, uint32_t* d_vals, size_t n, void* cuda_stream,
+                              void* d_workspace, size_t workspace_bytes) {
+    rs_status st = check_sort_args(d_keys, d_vals, n);
+    if (st != RS_OK || n == 0) return st;
+    if (d_workspace == nullptr || workspace_bytes < layout11(n, d_vals != nullptr).total)
+        return RS_ERR_INVALID_ARG;
+    return enqueue_sort11(d_keys, d_vals, (uint32_t)n, static_cast<cudaStream_t>(cuda_stream),
+                          d_workspace, workspace_bytes);
 }
 
 static rs_status seg_args(const uint32_t* keys, const uint32_t* vals, size_t n,

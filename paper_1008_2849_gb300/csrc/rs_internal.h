@@ -25,6 +25,9 @@ enum KernelKind : int {
     KK_SEG_SCAN = 6,
     KK_SEG_ONESWEEP = 7,
     KK_WARP = 8,
+    KK_D11_UP = 9,
+    KK_D11_SCAN = 10,
+    KK_D11_DOWN = 11,
     KK_COUNT
 };
 const char* kernel_kind_name(int kind);
@@ -97,7 +100,6 @@ Knobs& knobs();
 // Whether a typed sort of n items launches two instances of every scatter
 // pass (see Knobs::typed_split_min).
 inline bool typed_split(size_t n) { return n >= knobs().typed_split_min; }
-Knobs& knobs();
 
 // Host-side checks shared by the sort entry points: size, null pointers,
 // 4-byte alignment, keys and values not overlapping.
@@ -129,6 +131,18 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
 rs_status enqueue_msd_partition(const uint32_t* keys, const uint32_t* vals, uint32_t n,
                                 uint32_t* out_keys, uint32_t* out_vals, uint32_t* bucket_off,
                                 cudaStream_t stream, void* workspace, size_t workspace_bytes);
+
+// The sort with 11-bit digits (three passes of 11, 11 and 10 bits;
+// rs_digits11.cu): two alternate key (and value) buffers, per-chunk digit
+// counts of at most kD11MaxChunks chunks, and the 2048 bucket totals.
+constexpr uint32_t kD11MaxChunks = 1024;
+struct Layout11 {
+    size_t alt_keys[2], alt_vals[2], counts, totals, total;
+    uint32_t max_chunks;
+};
+Layout11 layout11(size_t n, bool pairs);
+rs_status enqueue_sort11(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
+                         void* workspace, size_t workspace_bytes);
 
 // Wide items: 64-bit keys (eight passes; key_type KEY_U64, KEY_I64 or
 // KEY_F64) carrying no, 32-bit or 64-bit values (val_bytes 0, 4 or 8), and

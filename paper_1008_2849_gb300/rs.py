@@ -38,6 +38,8 @@ SIGNATURES = {
     "rs_sort_pairs": (_int, [_vp, _vp, _sz]),
     "rs_sort_keys_ex": (_int, [_vp, _sz, _vp, _vp, _sz]),
     "rs_sort_pairs_ex": (_int, [_vp, _vp, _sz, _vp, _vp, _sz]),
+    "rs_sort_digits11_ex": (_int, [_vp, _vp, _sz, _vp, _vp, _sz]),
+    "rs_workspace_bytes_digits11": (_sz, [_sz, _int]),
     "rs_sort_keys_segmented": (_int, [_vp, _sz, _vp, _u32]),
     "rs_sort_pairs_segmented": (_int, [_vp, _vp, _sz, _vp, _u32]),
     "rs_sort_keys_segmented_ex": (_int, [_vp, _sz, _vp, _u32, _vp, _vp, _sz]),
@@ -168,6 +170,30 @@ def sort_pairs_ex(keys, vals, workspace, stream=None) -> None:
     _check(lib().rs_sort_pairs_ex(_dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel(),
                                   _stream_handle(stream), workspace.data_ptr(), workspace.numel()),
            "rs_sort_pairs_ex")
+
+
+def workspace_bytes_digits11(n: int, with_values: bool) -> int:
+    return int(lib().rs_workspace_bytes_digits11(int(n), 1 if with_values else 0))
+
+
+def alloc_workspace_digits11(n: int, with_values: bool, device=None):
+    """A 256-byte aligned torch uint8 CUDA tensor for sort_digits11_ex."""
+    import torch
+    nbytes = max(workspace_bytes_digits11(n, with_values), 1)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+    pad = (-ws.data_ptr()) % 256
+    return ws[pad:pad + nbytes]
+
+
+def sort_digits11_ex(keys, vals, workspace, stream=None) -> None:
+    """Enqueue the in-place sort with three passes of 11/11/10-bit digits
+    (vals None: keys only) on ``stream``."""
+    if vals is not None and vals.numel() != keys.numel():
+        raise ValueError("keys and vals differ in length")
+    vp = None if vals is None else _dev_ptr(vals, "vals")
+    _check(lib().rs_sort_digits11_ex(_dev_ptr(keys, "keys"), vp, keys.numel(),
+                                     _stream_handle(stream), workspace.data_ptr(),
+                                     workspace.numel()), "rs_sort_digits11_ex")
 
 
 def _segments(offsets):

@@ -93,6 +93,30 @@ def test_host_side_argument_errors(lib):
     assert lib.rs_sort_pairs_host_batch(tab, None, tab, None, big, 2) == 5     # n >= 2^32
 
 
+def test_workspace_bytes_digits11(lib):
+    from paper_1008_2849_gb300 import rs
+    assert rs.workspace_bytes_digits11(0, True) == 0
+    assert rs.workspace_bytes_digits11(1 << 32, True) == 0
+    for n in (1, 4095, 4097, 1_000_003, 1 << 28):
+        keys_only = rs.workspace_bytes_digits11(n, False)
+        pairs = rs.workspace_bytes_digits11(n, True)
+        # two alternate key (and value) buffers, per-chunk counts of at most
+        # 1024 chunks of 2048 buckets, the bucket totals, 256-byte rounding
+        assert 8 * n <= keys_only <= 8 * n + 1024 * 2048 * 4 + 8192 + 1024
+        assert 16 * n <= pairs <= 16 * n + 1024 * 2048 * 4 + 8192 + 2048
+        assert keys_only % 256 == 0 and pairs % 256 == 0
+    # Host-side refusals, before any CUDA call.
+    assert lib.rs_sort_digits11_ex(None, None, 5, None, ctypes.c_void_p(4096), 1 << 20) == 1
+    assert lib.rs_sort_digits11_ex(ctypes.c_void_p(4096), None, 100, None, None, 0) == 1
+    assert lib.rs_sort_digits11_ex(ctypes.c_void_p(4096), ctypes.c_void_p(4096 + 8), 100, None,
+                                   ctypes.c_void_p(1 << 20), 1 << 20) == 1     # overlap
+    assert lib.rs_sort_digits11_ex(ctypes.c_void_p(4096), None, 1 << 32, None,
+                                   ctypes.c_void_p(1 << 20), 1 << 20) == 5     # n >= 2^32
+    assert lib.rs_sort_digits11_ex(ctypes.c_void_p(4096), None, 100, None,
+                                   ctypes.c_void_p(1 << 20), 16) == 1          # too small
+    assert lib.rs_sort_digits11_ex(None, None, 0, None, None, 0) == 0          # nothing to do
+
+
 def test_workspace_bytes_kv(lib):
     from paper_1008_2849_gb300 import rs
     n = 1 << 20
