@@ -161,7 +161,10 @@ rs_status rs_sort_segmented_typed_ex(uint32_t* d_keys, uint32_t* d_vals, size_t 
 
 /* Bytes of device workspace an _ex call needs.  n = total items; with_values
  * = 0 for keys only, 1 for pairs; num_segments = 0 for the unsegmented calls,
- * else the number of segments of a segmented call.  Pure host arithmetic. */
+ * else the number of segments of a segmented call.  Pure host arithmetic.
+ * For an unsegmented sort whose size class has RS_TUNE_DIGITS = 11 it
+ * includes the buffers of the 11-bit order; a smaller workspace (down to the
+ * 8-bit order's) is still accepted and then takes the 8-bit order. */
 size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments);
 
 /* 64-bit keys: the same LSD radix sort with K = 64 and D = 8 (Sec. 4 leaves
@@ -381,13 +384,20 @@ typedef enum rs_tune_knob {
                                      launch two instances of every scatter pass (the passes that
                                      need no key map run without it, at the unsigned speed);
                                      smaller sorts launch one instance per pass, which maps where
-                                     needed (half the launches) */
+                                     needed (half the launches) */,
+    RS_TUNE_D11_SHAPE = 10,       /* tile shape of rs_sort_digits11_ex's scatter kernel: 0: 256
+                                     threads x 32 items, two CTAs per SM; 1: 512 x 32, one CTA
+                                     (the default); 2: 512 x 16, one CTA; 3: 256 x 24, two CTAs */
+    RS_TUNE_DIGITS = 11           /* 8 (the default): unsigned whole-array sorts run four 8-bit
+                                     passes; 11: three 11/11/10-bit passes (as
+                                     rs_sort_digits11_ex), taken when the caller's workspace holds
+                                     their buffers -- rs_workspace_bytes then includes them */
 } rs_tune_knob;
 
-/* Knobs 0, 1 and 4..8 are kept per size class of the item count -- the
+/* Knobs 0, 1, 4..8 and 11 are kept per size class of the item count -- the
  * whole array's, or for a segmented sort the average segment's: class 0 up
  * to 2^13 items, 1 up to 2^16, 2 up to 2^20, 3 up to 2^24, 4 up to 2^28,
- * 5 above.  Knobs 2, 3 and 9 are global. */
+ * 5 above.  Knobs 2, 3, 9 and 10 are global. */
 #define RS_NUM_SIZE_CLASSES 6
 
 /* Set a knob (a per-class knob in every class); RS_ERR_INVALID_ARG for an

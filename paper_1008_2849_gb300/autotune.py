@@ -7,7 +7,8 @@ under every candidate setting and keeps the fastest:
 
 * whole arrays: the tile shape of the scatter passes, for key-value and for
   keys-only sorts; up to 2^21 items, the MSD-first order of Alg. 2 (one pass
-  by the top digit, then on-chip bucket sorts) or the four LSD passes; for
+  by the top digit, then on-chip bucket sorts) or the four LSD passes; from
+  2^24 items, four passes of 8-bit digits or three of 11/11/10 bits; for
   arrays up to 8192 items, which take the one-CTA sort, and at which digit
   width;
 * segmented batches: the tile shape of the segmented scatter passes and the
@@ -15,8 +16,7 @@ under every candidate setting and keeps the fastest:
   short arrays the largest segment sorted by the one-warp sort and the digit
   width of the on-chip sorts (4 bits, eight passes, or 8 bits, four passes).
 
-The scatter passes of large arrays keep 8-bit digits (four passes over
-32-bit keys).  Results never depend on the settings, only speed does.  The table is JSON:
+Results never depend on the settings, only speed does.  The table is JSON:
 
     {"device": "...", "classes": {"3": {"tile_pairs": 3, "tile_keys": 3, ...}}}
 
@@ -34,6 +34,7 @@ import numpy as np
 # Representative item counts per size class (whole arrays).
 CLASS_SIZES = {1: 1 << 16, 2: 1 << 20, 3: 1 << 24, 4: 1 << 27}
 MSD_MAX_ITEMS = 256 * 8192  # largest whole array the MSD-first order is tried for
+DIGITS11_MIN_ITEMS = 1 << 24  # smallest whole array the 11-bit-digit order is tried for
 
 
 def _time_graph(rs, torch, graph, restore, reps):
@@ -64,7 +65,9 @@ def tune_whole(rs, torch, inputs, reps=3, quick=False):
         v = torch.arange(n, dtype=torch.int32, device="cuda")
         kb, vb = torch.empty_like(k), torch.empty_like(v)
         best = {}
-        saved = {kn: rs.tune_get_class(cls, kn) for kn in ("tile_pairs", "tile_keys", "msd")}
+        saved = {kn: rs.tune_get_class(cls, kn)
+                 for kn in ("tile_pairs", "tile_keys", "msd", "digits")}
+        rs.tune_set_class(cls, "digits", 8)  # shapes are timed on the 8-bit passes
         rs.tune_set_class(cls, "msd", 0)  # shapes are timed on the four LSD passes
         for pairs in (True, False):
             knob = "tile_pairs" if pairs else "tile_keys"
@@ -102,7 +105,24 @@ def tune_whole(rs, torch, inputs, reps=3, quick=False):
             rs.tune_set_class(cls, "msd", old_msd)
             best["msd"] = min(res, key=res.get)
             best["msd_ms"] = res
-        for knob in ("tile_pairs", "tile_keys", "msd"):
+        if n >= DIGITS11_MIN_ITEMS:
+            # Four 8-bit passes or three 11/11/10-bit ones (the graph's
+            # workspace holds the latter's buffers when the class takes them).
+            res = {}
+            for digits in (8, 11):
+                rs.tune_set_class(cls, "digits", digits)
+                tot = 0.0
+                for pairs in (True, False):
+                    def restore():
+                        kb.copy_(k)
+                        vb.copy_(v)
+                    g = rs.Graph(kb, vb if pairs else None)
+                    tot += _time_graph(rs, torch, g, restore, reps)
+                    g.close()
+                res[digits] = tot
+            best["digits"] = min(res, key=res.get)
+            best["digits_ms"] = res
+        for knob in ("tile_pairs", "tile_keys", "msd", "digits"):
             rs.tune_set_class(cls, knob, saved[knob])
         out[str(cls)] = best
         del k, v, kb, vb
@@ -209,7 +229,7 @@ def apply(table: dict) -> None:
     from paper_1008_2849_gb300 import rs
     for cls, knobs in table.get("classes", {}).items():
         for name in ("tile_pairs", "tile_keys", "tile_seg", "small_max", "warp_max", "small_bits",
-                     "msd"):
+                     "msd", "digits"):
             if name in knobs:
                 rs.tune_set_class(int(cls), name, int(knobs[name]))
 

@@ -25,6 +25,11 @@
    23): 32-bit keys with 64-bit values (four passes), 64-bit keys (unsigned
    and IEEE binary64) with 64-bit values and signed 64-bit keys alone (eight
    passes).
+6. Digit width of the whole-array sort: four 8-bit passes (rs_sort_pairs_ex,
+   rs_sort_keys_ex) against three 11/11/10-bit passes (rs_sort_digits11_ex)
+   with every tile shape of its scatter kernel, pairs and keys only of
+   2^20..2^28 uniform keys (seed 25), each step on a fresh copy; with the
+   device time of each of its kernels (rs_profile_*) for the default shape.
 
 Prints one JSON line.
 """
@@ -238,8 +243,60 @@ def main(argv=None) -> int:
             "scatter_tb_per_s": n * per_pass * passes / (ms / 1e3) / 1e12}
         del k, kb, vb, ws, raw
     out["items_2^27_wide"] = wide
+    del i64
+
+    # 6. four 8-bit passes against three 11/11/10-bit ones.
+    out["digits11_vs_8"] = _digits_sweep(torch, rs, inputs, stream, a)
     print(json.dumps(out), flush=True)
     return 0
+
+
+def _digits_sweep(torch, rs, inputs, stream, a):
+    rows = {}
+    old = rs.tune_get("d11_shape")
+    try:
+        for lg in (20, 22, 24, 26, 28):
+            n = 1 << lg
+            k = inputs.keys_torch("uniform", n, seed=25)
+            v = torch.arange(n, dtype=torch.int32, device="cuda")
+            kb, vb = torch.empty_like(k), torch.empty_like(v)
+
+            def restore():
+                kb.copy_(k)
+                vb.copy_(v)
+            for pairs in (True, False):
+                row = {}
+                ws = rs.alloc_workspace(n, pairs)
+                if pairs:
+                    fn8 = lambda: rs.sort_pairs_ex(kb, vb, ws, stream)  # noqa: E731
+                else:
+                    fn8 = lambda: rs.sort_keys_ex(kb, ws, stream)  # noqa: E731
+                row["digits8_ms"] = _timed(torch, stream, fn8, restore, a.steps, a.warmup)
+                del ws
+                ws = rs.alloc_workspace_digits11(n, pairs)
+                vv = vb if pairs else None
+                for shape in range(4):
+                    rs.tune_set("d11_shape", shape)
+                    row["digits11_shape%d_ms" % shape] = _timed(
+                        torch, stream, lambda: rs.sort_digits11_ex(kb, vv, ws, stream), restore,
+                        a.steps, a.warmup)
+                rs.tune_set("d11_shape", old)
+                restore()
+                rs.profile_enable(True)
+                rs.profile_read()
+                rs.sort_digits11_ex(kb, vv, ws, stream)
+                torch.cuda.synchronize()
+                prof = rs.profile_read()
+                rs.profile_enable(False)
+                row["digits11_kernels_ms"] = {kind: ms for kind, (cnt, ms) in prof.items() if cnt}
+                rs.check_stream()
+                rows["%s_2^%d" % ("pairs" if pairs else "keys", lg)] = row
+                del ws
+            del k, v, kb, vb
+            torch.cuda.empty_cache()
+    finally:
+        rs.tune_set("d11_shape", old)
+    return rows
 
 
 def _typed_split_sweep(torch, rs, inputs, stream, a):

@@ -2,6 +2,7 @@
 // include/rs.h): argument checks, workspace handling for the plain calls,
 // the host-buffer path, the sticky device status word, launch counting and
 // optional per-kernel event timing.
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -146,7 +147,7 @@ rs_status plain_sort(uint32_t* keys, uint32_t* vals, size_t n) {
     st = device_info_for(dev, &di);
     if (st != RS_OK) return st;
     DevState& d = g_dev[dev];
-    st = ensure_workspace_locked(d, layout_for(n, vals != nullptr).total);
+    st = ensure_workspace_locked(d, sort_workspace_bytes(n, vals != nullptr));
     if (st != RS_OK) return st;
     st = enqueue_sort(keys, vals, (uint32_t)n, cudaStreamLegacy, d.ws, d.ws_bytes);
     if (st != RS_OK) return st;
@@ -154,6 +155,15 @@ rs_status plain_sort(uint32_t* keys, uint32_t* vals, size_t n) {
 }
 
 }  // namespace
+
+size_t sort_workspace_bytes(size_t n, bool pairs) {
+    size_t t = layout_for(n, pairs).total;
+    if (n > 0 && n < (size_t(1) << 32) && knobs().cls[size_class(n)].digits == 11) {
+        const size_t t11 = layout11(n, pairs).total;
+        if (t11 > t) t = t11;
+    }
+    return t;
+}
 
 rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n) {
     if (n >= (size_t(1) << 32)) return RS_ERR_UNSUPPORTED;
@@ -174,12 +184,15 @@ Knobs& knobs() {
     // 12); larger ones shape 3 (384 x 13, two CTAs per SM), and for keys only
     // shape 6 (384 x 18: no value buffer, still two CTAs).
     // Per class:
-    // {tile_pairs, tile_keys, tile_seg, small_max, warp_max, small_bits, msd}.
+    // {tile_pairs, tile_keys, tile_seg, small_max, warp_max, small_bits, msd,
+    //  digits}.
     // The MSD-first order measured faster only up to 2^16 items (class 1).
-    static Knobs k{{{1, 1, 3, 8192, 512, 8, 0}, {4, 1, 3, 4096, 512, 8, 1},
-                    {1, 1, 3, 4096, 512, 8, 0}, {3, 6, 3, 4096, 512, 8, 0},
-                    {3, 6, 3, 4096, 512, 8, 0}, {3, 6, 3, 4096, 512, 8, 0}},
-                   kDefaultSpinLimit, 0, 4, 3, kDefaultTypedSplitMin};
+    // The 11-bit-digit order (three passes) measured slower in every class
+    // (2.3 to 2.8 times the 8-bit sort at 2^24 to 2^28 pairs), so it is off.
+    static Knobs k{{{1, 1, 3, 8192, 512, 8, 0, 8}, {4, 1, 3, 4096, 512, 8, 1, 8},
+                    {1, 1, 3, 4096, 512, 8, 0, 8}, {3, 6, 3, 4096, 512, 8, 0, 8},
+                    {3, 6, 3, 4096, 512, 8, 0, 8}, {3, 6, 3, 4096, 512, 8, 0, 8}},
+                   kDefaultSpinLimit, 0, 4, 3, kDefaultTypedSplitMin, 1};
     return k;
 }
 
@@ -368,7 +381,7 @@ rs_status rs_sort_pairs_segmented_ex(uint32_t* d_keys, uint32_t* d_vals, size_t 
 size_t rs_workspace_bytes(size_t n, int with_values, uint32_t num_segments) {
     if (n == 0) return 0;
     if (num_segments > 0) return seg_layout_for(n, with_values != 0, num_segments).total;
-    return layout_for(n, with_values != 0).total;
+    return sort_workspace_bytes(n, with_values != 0);
 }
 
 size_t rs_workspace_bytes64(size_t n, int with_values) {
@@ -563,7 +576,7 @@ rs_status rs_sort_pairs_host(const uint32_t* h_keys_in, const uint32_t* h_vals_i
         }
         d.h_cap = n;
     }
-    st = ensure_workspace_locked(d, layout_for(n, pairs).total);
+    st = ensure_workspace_locked(d, sort_workspace_bytes(n, pairs));
     if (st != RS_OK) return st;
     const size_t bytes = n * 4;
     // A failure part-way waits for the work already enqueued, so that no copy
@@ -652,7 +665,10 @@ rs_status rs_sort_pairs_host_batch(const uint32_t* const* h_keys_in,
             }
         d.b_cap = nmax;
     }
-    st = ensure_workspace_locked(d, layout_for(nmax, pairs).total);
+    size_t ws_need = 0;
+    for (uint32_t i = 0; i < count; ++i)
+        if (n[i] > 0) ws_need = std::max(ws_need, sort_workspace_bytes(n[i], pairs));
+    st = ensure_workspace_locked(d, ws_need);
     if (st != RS_OK) return st;
     // Array i uses buffer set i % kHostSets.  Its upload waits for the
     // download of the array that used the set before; its sort (one compute
@@ -824,6 +840,10 @@ static rs_status set_class_knob(ClassKnobs& c, int knob, int value) {
         if (value != 0 && value != 1) return RS_ERR_INVALID_ARG;
         c.msd = value;
         return RS_OK;
+    case 11:
+        if (value != 8 && value != 11) return RS_ERR_INVALID_ARG;
+        c.digits = value;
+        return RS_OK;
     default: return RS_ERR_INVALID_ARG;
     }
 }
@@ -837,6 +857,7 @@ static int get_class_knob(const ClassKnobs& c, int knob) {
     case 6: return c.warp_max;
     case 7: return c.small_bits;
     case 8: return c.msd;
+    case 11: return c.digits;
     default: return -1;
     }
 }
@@ -856,6 +877,10 @@ rs_status rs_tune_set(int knob, int value) {
         if (value < 0) return RS_ERR_INVALID_ARG;
         k.typed_split_min = (uint32_t)value;
         return RS_OK;
+    case 10:
+        if (value < 0 || value >= d11_shape_count()) return RS_ERR_INVALID_ARG;
+        k.d11_shape = value;
+        return RS_OK;
     default:
         for (int c = 0; c < NUM_SIZE_CLASSES; ++c) {
             rs_status st = set_class_knob(k.cls[c], knob, value);
@@ -871,6 +896,7 @@ int rs_tune_get(int knob) {
     case 2: return k.hist_ctas_per_sm;
     case 3: return k.hist_mode;
     case 9: return (int)(k.typed_split_min > 0x7fffffffu ? 0x7fffffffu : k.typed_split_min);
+    case 10: return k.d11_shape;
     default: return get_class_knob(k.cls[4], knob);
     }
 }

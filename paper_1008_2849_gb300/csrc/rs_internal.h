@@ -75,6 +75,8 @@ struct ClassKnobs {
     int warp_max;
     int small_bits;
     int msd;        // 1: whole arrays up to kMsdMaxItems may take the MSD-first order
+    int digits;     // 8: four 8-bit passes; 11: three 11/11/10-bit passes (rs_digits11.cu)
+                    // for unsigned keys, when the caller's workspace holds their buffers
 };
 // Largest whole array the MSD-first order is tried for: 256 buckets of at
 // most the one-CTA sort's capacity.
@@ -95,6 +97,7 @@ struct Knobs {
     // every scatter pass (the passes that need no key map run without it);
     // smaller ones launch only the mapping instance, which runs every pass.
     uint32_t typed_split_min;
+    int d11_shape;           // tile shape of the 11-bit-digit sort's scatter kernel
 };
 Knobs& knobs();
 // Whether a typed sort of n items launches two instances of every scatter
@@ -119,6 +122,9 @@ struct Layout {
     bool wide_status;        // 64-bit status words (n >= 2^30)
 };
 Layout layout_for(size_t n, bool pairs);
+// Workspace of the whole-array sorts of n items: the 8-bit layout, or the
+// 11-bit one's when n's size class takes that order and it is larger.
+size_t sort_workspace_bytes(size_t n, bool pairs);
 
 // Enqueue the whole sort of n items (1 <= n < 2^32) on `stream`, using the
 // caller's workspace (at least layout_for(n, pairs).total bytes).
@@ -141,6 +147,7 @@ struct Layout11 {
     uint32_t max_chunks;
 };
 Layout11 layout11(size_t n, bool pairs);
+int d11_shape_count();
 rs_status enqueue_sort11(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t stream,
                          void* workspace, size_t workspace_bytes);
 

@@ -151,6 +151,10 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     if (n <= (uint32_t)ck.small_max && n <= small_sort_capacity())
         return launch_small_sort(keys, vals, nullptr, nullptr, nullptr, n, n, ck.small_bits,
                                  key_type, stream);
+    // Three passes of 11/11/10-bit digits, where the size class takes them
+    // and the caller's workspace holds their buffers.
+    if (ck.digits == 11 && key_type == KEY_U32 && workspace_bytes >= layout11(n, pairs).total)
+        return enqueue_sort11(keys, vals, n, stream, workspace, workspace_bytes);
     char* ws = static_cast<char*>(workspace);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
     void* status[2] = {ws + L.status0, ws + L.status1};

@@ -1,14 +1,17 @@
 """One sort of a seeded synthetic array, for profiler captures.
 
     python -m paper_1008_2849_gb300.profile_case --log2n 26 [--keys-only]
-           [--dist uniform] [--seed 2] [--repeat 1]
+           [--dist uniform] [--seed 2] [--repeat 1] [--digits11 SHAPE]
 
 Builds librs.so if needed, copies the input to the GPU, runs rs_sort_pairs_ex
 (or rs_sort_keys_ex) `repeat` times on fresh copies and checks the device
 status.  It times nothing: a profiler (ncu) around it sees exactly the
 library's kernels (per sort: one histogram, one plan and four scatter-pass
-launches).  2^26 pairs is 512 MiB per array, more than the L2, and small
-enough for a many-pass capture to finish quickly.
+launches).  With --digits11 SHAPE it runs rs_sort_digits11_ex instead (three
+passes of 11/11/10-bit digits, scatter-kernel tile shape SHAPE; per sort:
+three counting, three scan and three scatter launches).  2^26 pairs is 256
+MiB per array, more than the L2, and small enough for a many-pass capture to
+finish quickly.
 """
 from __future__ import annotations
 
@@ -26,6 +29,8 @@ def main(argv=None) -> int:
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--digits11", type=int, default=-1,
+                    help="tile shape of the 11-bit-digit sort; -1: the default sort")
     a = ap.parse_args(argv)
 
     import torch
@@ -37,11 +42,17 @@ def main(argv=None) -> int:
     k = torch.from_numpy(inputs.keys(a.dist, n, a.seed).view(np.int32)).cuda()
     v = torch.arange(n, dtype=torch.int32, device="cuda")
     kb, vb = torch.empty_like(k), torch.empty_like(v)
-    ws = rs.alloc_workspace(n, not a.keys_only)
+    if a.digits11 >= 0:
+        rs.tune_set("d11_shape", a.digits11)
+        ws = rs.alloc_workspace_digits11(n, not a.keys_only)
+    else:
+        ws = rs.alloc_workspace(n, not a.keys_only)
     for _ in range(a.repeat):
         kb.copy_(k)
         vb.copy_(v)
-        if a.keys_only:
+        if a.digits11 >= 0:
+            rs.sort_digits11_ex(kb, None if a.keys_only else vb, ws)
+        elif a.keys_only:
             rs.sort_keys_ex(kb, ws)
         else:
             rs.sort_pairs_ex(kb, vb, ws)

@@ -73,6 +73,27 @@ def test_digits11_unaligned(rs, off_elems):
     assert np.array_equal(to_host(kd), ko) and np.array_equal(to_host(vd), vo)
 
 
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+@pytest.mark.parametrize("n", [5000, 1_000_003])
+def test_digits11_every_tile_shape(rs, shape, n):
+    """Every tile shape of the scatter kernel (RS_TUNE_D11_SHAPE), pairs and
+    keys only."""
+    old = rs.tune_get("d11_shape")
+    rs.tune_set("d11_shape", shape)
+    try:
+        k = inputs.keys("and2", n, seed=640 + shape)
+        v = inputs.index_values(n)
+        kd, vd, kk = to_dev(k), to_dev(v), to_dev(k)
+        rs.sort_digits11_ex(kd, vd, rs.alloc_workspace_digits11(n, True))
+        rs.sort_digits11_ex(kk, None, rs.alloc_workspace_digits11(n, False))
+        rs.check_stream()
+    finally:
+        rs.tune_set("d11_shape", old)
+    ko, vo = oracle_sort(k, v)
+    assert np.array_equal(to_host(kd), ko) and np.array_equal(to_host(vd), vo)
+    assert np.array_equal(to_host(kk), ko)
+
+
 def test_digits11_workspace_errors(rs):
     import torch
     kd = to_dev(np.arange(1000, dtype=np.uint32))
@@ -111,3 +132,53 @@ def test_digits11_full_size_properties(rs):
     srt = np.sort(host)
     pos = (inputs.splitmix32(631, 4096, 0).astype(np.int64) * n) >> 32
     assert np.array_equal(ku[torch.from_numpy(pos).cuda()].cpu().numpy(), srt[pos])
+
+
+@pytest.mark.parametrize("pairs", [True, False])
+def test_digits_knob_routes_the_plain_sorts(rs, pairs):
+    """RS_TUNE_DIGITS = 11 in the array's size class: the plain call, the
+    _ex call with a workspace from rs_workspace_bytes, and a captured graph
+    all run the three 11/11/10-bit passes (their kernels are the ones that
+    launch) and equal the oracle; with an 8-bit-sized workspace the _ex call
+    takes the 8-bit passes, with the same result."""
+    n = 1_000_003
+    cls = rs.size_class(n)
+    k = inputs.keys("uniform", n, seed=650 + pairs)
+    v = inputs.index_values(n)
+    ko, vo = oracle_sort(k, v)
+    old = rs.tune_get_class(cls, "digits")
+    rs.profile_enable(True)
+    try:
+        small_ws = rs.alloc_workspace(n, pairs)  # sized for the 8-bit order
+        rs.tune_set_class(cls, "digits", 11)
+        outs = []
+        for how in ("plain", "ex", "graph", "ex_small"):
+            kd, vd = to_dev(k), to_dev(v)
+            rs.profile_read()
+            launches = rs.launch_count()
+            if how == "plain":
+                rs.sort_pairs(kd, vd) if pairs else rs.sort_keys(kd)
+            elif how in ("ex", "ex_small"):
+                ws = small_ws if how == "ex_small" else rs.alloc_workspace(n, pairs)
+                rs.sort_pairs_ex(kd, vd, ws) if pairs else rs.sort_keys_ex(kd, ws)
+            else:
+                g = rs.Graph(kd, vd if pairs else None)
+                g.launch()
+                g.close()
+            rs.check_stream()
+            prof = rs.profile_read()
+            launched = rs.launch_count() - launches
+            if how == "graph":  # replays are counted, not timed per kernel
+                assert launched == 9, launched  # 3 x (count, scan, scatter)
+            elif how == "ex_small":
+                assert "d11_down" not in prof or prof["d11_down"][0] == 0, prof
+            else:
+                assert prof["d11_down"][0] == 3 and launched == 9, (how, prof, launched)
+            outs.append((how, to_host(kd), to_host(vd)))
+    finally:
+        rs.profile_enable(False)
+        rs.tune_set_class(cls, "digits", old)
+    for how, ok_, ov_ in outs:
+        assert np.array_equal(ok_, ko), how
+        if pairs:
+            assert np.array_equal(ov_, vo), how

@@ -67,7 +67,7 @@ def test_knob_table_matches_header(rs):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     text = open(os.path.join(root, "include", "rs.h")).read()
     header = {m.group(1).lower(): int(m.group(2))
-              for m in re.finditer(r"RS_TUNE_([A-Z_]+)\s*=\s*(\d+)", text)}
+              for m in re.finditer(r"RS_TUNE_([A-Z0-9_]+)\s*=\s*(\d+)", text)}
     assert header == rs.TUNE_KNOBS
 
 
@@ -88,3 +88,27 @@ def test_on_chip_sort_knobs_are_checked(rs):
     finally:
         for c, k, v in saved:
             rs.tune_set_class(c, k, v)
+
+
+def test_digits_knob_sizes_the_workspace(rs):
+    """RS_TUNE_DIGITS = 11 in a size class makes rs_workspace_bytes cover the
+    11-bit order's buffers for that class only; 8 restores the 8-bit size."""
+    n4, n3 = 1 << 26, 1 << 22  # classes 4 and 3
+    base4, base3 = rs.workspace_bytes(n4, True), rs.workspace_bytes(n3, True)
+    old = rs.tune_get_class(4, "digits")
+    assert old == 8
+    try:
+        rs.tune_set_class(4, "digits", 11)
+        assert rs.workspace_bytes(n4, True) == max(base4, rs.workspace_bytes_digits11(n4, True))
+        assert rs.workspace_bytes(n4, True) > base4
+        assert rs.workspace_bytes(n3, True) == base3
+        for bad in (0, 4, 9, 12):
+            with pytest.raises(rs.RsError):
+                rs.tune_set_class(4, "digits", bad)
+    finally:
+        rs.tune_set_class(4, "digits", old)
+    assert rs.workspace_bytes(n4, True) == base4
+    assert rs.tune_get("d11_shape") == 1
+    for bad in (-1, 4):
+        with pytest.raises(rs.RsError):
+            rs.tune_set("d11_shape", bad)
