@@ -60,7 +60,7 @@ WORKLOAD = "sort_pairs_u32_2^28_uniform"
 ONESWEEP_SOURCES = ("paper_1008_2849_gb300/csrc/rs_onesweep.cuh",
                     "paper_1008_2849_gb300/csrc/rs_onesweep_launch.cuh",
                     "paper_1008_2849_gb300/csrc/rs_device.cuh",
-                    "paper_1008_2849_gb300/csrc/rs_internal.h")  # tile shapes
+                    "paper_1008_2849_gb300/csrc/rs_internal.h:RS_TILE_SHAPES")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pairs_2^28_traffic.txt")
 
 
@@ -103,14 +103,24 @@ def measured_peaks():
 
 def source_hash(paths) -> str:
     """Hash of the code in `paths`: line comments, trailing blanks and blank
-    lines are left out, so that editing a comment keeps the hash."""
+    lines are left out, so that editing a comment keeps the hash.  A path
+    written "file:MACRO" stands for the definition of that macro only (its
+    #define line and the continuation lines after it)."""
     h = hashlib.sha256()
     for p in paths:
-        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
-            for line in f:
-                code = line.split("//", 1)[0].rstrip()
-                if code:
-                    h.update(code.encode() + b"\n")
+        path, _, macro = p.partition(":")
+        with open(os.path.join(ROOT, path), encoding="utf-8") as f:
+            lines = f.read().splitlines()
+        if macro:
+            start = next(i for i, ln in enumerate(lines) if ln.startswith("#define " + macro))
+            end = start
+            while lines[end].rstrip().endswith("\\"):
+                end += 1
+            lines = lines[start:end + 1]
+        for line in lines:
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

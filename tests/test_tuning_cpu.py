@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import json
+import os
 
 import pytest
 
@@ -112,3 +113,37 @@ def test_digits_knob_sizes_the_workspace(rs):
     for bad in (-1, 4):
         with pytest.raises(rs.RsError):
             rs.tune_set("d11_shape", bad)
+
+
+def test_traffic_record_follows_the_kernel_source(tmp_path):
+    """bench.py's recorded ncu traffic is used only while the scatter kernel's
+    code is the code it was captured from: comment edits and unrelated header
+    lines keep the source hash, code and tile-shape edits change it; the
+    committed record matches the current sources."""
+    import shutil
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    assert bench.recorded_traffic() is not None
+    for p in bench.ONESWEEP_SOURCES:
+        path = p.split(":")[0]
+        (tmp_path / os.path.dirname(path)).mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(root, path), tmp_path / path)
+    old_root = bench.ROOT
+    bench.ROOT = str(tmp_path)
+    try:
+        base = bench.source_hash(bench.ONESWEEP_SOURCES)
+        hdr = tmp_path / "paper_1008_2849_gb300/csrc/rs_internal.h"
+        kern = tmp_path / "paper_1008_2849_gb300/csrc/rs_onesweep.cuh"
+        text_h, text_k = hdr.read_text(), kern.read_text()
+        hdr.write_text(text_h + "\n// a comment\nconstexpr int kUnrelated = 3;\n")
+        kern.write_text(text_k.replace("#pragma once", "#pragma once  // a comment", 1))
+        assert bench.source_hash(bench.ONESWEEP_SOURCES) == base
+        hdr.write_text(text_h.replace("X(3, 384, 13, 2, 6)", "X(3, 384, 12, 2, 6)"))
+        assert bench.source_hash(bench.ONESWEEP_SOURCES) != base
+        hdr.write_text(text_h)
+        kern.write_text(text_k.replace("#pragma once", "#pragma once\nstatic int x_;", 1))
+        assert bench.source_hash(bench.ONESWEEP_SOURCES) != base
+    finally:
+        bench.ROOT = old_root
