@@ -62,6 +62,7 @@ ONESWEEP_SOURCES = ("paper_1008_2849_gb300/csrc/rs_onesweep.cuh",
                     "paper_1008_2849_gb300/csrc/rs_device.cuh",
                     "paper_1008_2849_gb300/csrc/rs_internal.h:RS_TILE_SHAPES")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pairs_2^28_traffic.txt")
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal; the roofline's peak is the measured copy rate
 
 
 def dist_env():
@@ -462,6 +463,8 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic,
             "kernel": "k_onesweep (pairs, default tile shape)", "peak_source": peak_src + " (hbm_gbs, copy)",
+            "nominal_peak": NOMINAL_HBM_GBS,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS if achieved else None,
             "avg_launch_ms": os_ms / os_launches if os_launches else None,
             "algorithmic_bytes_per_launch": algo_bytes,
             "hist_avg_launch_ms": hist_ms / hist_launches if hist_launches else None,
