@@ -97,3 +97,22 @@ def test_pairs_max_size(rs):
     assert bool(seen.all())
     del k, v, orig, seen
     torch.cuda.empty_cache()
+
+
+def test_digits11_keys_max_size(rs):
+    """The 11/11/10-bit sort at n = 2^32 - 1 keys (two alternate buffers of
+    16 GiB in the workspace; chunk offsets, tile bases and output slots at
+    their 32-bit limits)."""
+    import torch
+    k = _draw(torch, 302)
+    h_in = rs.digit_histograms(k).clone()
+    s_in = _sums(torch, k)
+    ws = rs.alloc_workspace_digits11(N, False)
+    rs.sort_digits11_ex(k, None, ws)
+    rs.check_stream()
+    del ws
+    _nondecreasing(torch, k)
+    assert torch.equal(rs.digit_histograms(k), h_in)
+    assert _sums(torch, k) == s_in
+    del k
+    torch.cuda.empty_cache()
