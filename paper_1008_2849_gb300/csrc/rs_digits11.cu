@@ -339,7 +339,10 @@ struct D11Launch {
 constexpr D11Launch kD11Shapes[] = {RS_D11_SHAPES(RS_D11_INFO)};
 #undef RS_D11_INFO
 constexpr uint32_t kNumD11Shapes = sizeof(kD11Shapes) / sizeof(kD11Shapes[0]);
-constexpr uint32_t kD11MinTile = 4096;  // smallest tile of RS_D11_SHAPES (layout sizing)
+// Layout sizing: no larger than the smallest tile of RS_D11_SHAPES, so that
+// the counts buffer holds a chunk per tile of any shape.
+constexpr uint32_t kD11MinTile = 4096;
+static_assert(kD11MinTile <= 256 * 24, "every shape's tile is at least kD11MinTile items");
 
 template <uint32_t T, uint32_t J, uint32_t B, bool PAIRS>
 rs_status launch_down(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, uint32_t* dv,
