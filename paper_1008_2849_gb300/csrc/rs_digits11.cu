@@ -342,7 +342,13 @@ constexpr uint32_t kNumD11Shapes = sizeof(kD11Shapes) / sizeof(kD11Shapes[0]);
 // Layout sizing: no larger than the smallest tile of RS_D11_SHAPES, so that
 // the counts buffer holds a chunk per tile of any shape.
 constexpr uint32_t kD11MinTile = 4096;
-static_assert(kD11MinTile <= 256 * 24, "every shape's tile is at least kD11MinTile items");
+constexpr uint32_t smallest_d11_tile() {
+    uint32_t m = kD11Shapes[0].tile;
+    for (uint32_t i = 1; i < kNumD11Shapes; ++i)
+        if (kD11Shapes[i].tile < m) m = kD11Shapes[i].tile;
+    return m;
+}
+static_assert(kD11MinTile <= smallest_d11_tile(), "every shape's tile is at least kD11MinTile");
 
 template <uint32_t T, uint32_t J, uint32_t B, bool PAIRS>
 rs_status launch_down(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, uint32_t* dv,
