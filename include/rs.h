@@ -388,16 +388,20 @@ typedef enum rs_tune_knob {
     RS_TUNE_D11_SHAPE = 10,       /* tile shape of rs_sort_digits11_ex's scatter kernel: 0: 256
                                      threads x 32 items, two CTAs per SM; 1: 512 x 32, one CTA
                                      (the default); 2: 512 x 16, one CTA; 3: 256 x 24, two CTAs */
-    RS_TUNE_DIGITS = 11           /* 8 (the default): unsigned whole-array sorts run four 8-bit
+    RS_TUNE_DIGITS = 11,          /* 8 (the default): unsigned whole-array sorts run four 8-bit
                                      passes; 11: three 11/11/10-bit passes (as
                                      rs_sort_digits11_ex), taken when the caller's workspace holds
                                      their buffers -- rs_workspace_bytes then includes them */
+    RS_TUNE_PDL = 13              /* 1 (the default): the plan and scatter-pass kernels launch as
+                                     programmatic dependents of the kernel before them (resident
+                                     while it finishes, waiting on the device for its results);
+                                     0: plain stream order */
 } rs_tune_knob;
 
 /* Knobs 0, 1, 4..8 and 11 are kept per size class of the item count -- the
  * whole array's, or for a segmented sort the average segment's: class 0 up
  * to 2^13 items, 1 up to 2^16, 2 up to 2^20, 3 up to 2^24, 4 up to 2^28,
- * 5 above.  Knobs 2, 3, 9 and 10 are global. */
+ * 5 above.  Knobs 2, 3, 9, 10 and 13 are global. */
 #define RS_NUM_SIZE_CLASSES 6
 
 /* Set a knob (a per-class knob in every class); RS_ERR_INVALID_ARG for an

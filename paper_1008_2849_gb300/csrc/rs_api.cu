@@ -192,7 +192,7 @@ Knobs& knobs() {
     static Knobs k{{{1, 1, 3, 8192, 512, 8, 0, 8}, {4, 1, 3, 4096, 512, 8, 1, 8},
                     {1, 1, 3, 4096, 512, 8, 0, 8}, {3, 6, 3, 4096, 512, 8, 0, 8},
                     {3, 6, 3, 4096, 512, 8, 0, 8}, {3, 6, 3, 4096, 512, 8, 0, 8}},
-                   kDefaultSpinLimit, 0, 4, 3, kDefaultTypedSplitMin, 1};
+                   kDefaultSpinLimit, 0, 4, 3, kDefaultTypedSplitMin, 1, 1};
     return k;
 }
 
@@ -881,6 +881,10 @@ rs_status rs_tune_set(int knob, int value) {
         if (value < 0 || value >= d11_shape_count()) return RS_ERR_INVALID_ARG;
         k.d11_shape = value;
         return RS_OK;
+    case 13:
+        if (value != 0 && value != 1) return RS_ERR_INVALID_ARG;
+        k.pdl = value;
+        return RS_OK;
     default:
         for (int c = 0; c < NUM_SIZE_CLASSES; ++c) {
             rs_status st = set_class_knob(k.cls[c], knob, value);
@@ -897,6 +901,7 @@ int rs_tune_get(int knob) {
     case 3: return k.hist_mode;
     case 9: return (int)(k.typed_split_min > 0x7fffffffu ? 0x7fffffffu : k.typed_split_min);
     case 10: return k.d11_shape;
+    case 13: return k.pdl;
     default: return get_class_knob(k.cls[4], knob);
     }
 }

@@ -214,6 +214,18 @@ __device__ __forceinline__ void named_barrier_sync(uint32_t id, uint32_t count) 
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialization attribute (launch_after_previous) may become resident
+// while the kernel before it on the stream is still running; pdl_wait()
+// returns once that kernel has completed and its writes are visible, and
+// must come before anything that reads them.  (Launched without the
+// attribute, the kernel starts after its predecessor and pdl_wait() returns
+// at once.)  pdl_launch_next() lets the next such kernel start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void record_error(Ctrl* ctrl, uint32_t* sticky, uint32_t bits) {
     atomicOr(&ctrl->err, bits);
     atomicOr(sticky, bits);

@@ -123,6 +123,7 @@ k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
     uint32_t* const s_col = reinterpret_cast<uint32_t*>(s_cols4);
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31;
+    pdl_launch_next();  // the plan kernel may launch; it waits for this one
     for (uint32_t i = tid; i < HIST_COL_WORDS / 4; i += THREADS) s_cols4[i] = make_uint4(0, 0, 0, 0);
     const uint32_t gtid = blockIdx.x * THREADS + tid;
     const uint32_t gsize = gridDim.x * THREADS;
@@ -194,6 +195,8 @@ k_plan(Ctrl* __restrict__ ctrl, uint32_t n, uint32_t msd_allowed, uint32_t warp_
     __shared__ uint32_t s_big;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t b = tid & (RADIX - 1);
+    pdl_launch_next();
+    pdl_wait();  // the histograms are complete
     if (tid < NPASS) s_trivial[tid] = 0;
     if (tid == 0) s_big = 0;
     // Thread (p, b): p = tid / 256 (+ 4 in the second round for 64-bit keys).

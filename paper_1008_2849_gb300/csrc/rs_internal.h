@@ -4,6 +4,7 @@
 #pragma once
 
 #include <atomic>
+#include <utility>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -98,6 +99,7 @@ struct Knobs {
     // smaller ones launch only the mapping instance, which runs every pass.
     uint32_t typed_split_min;
     int d11_shape;           // tile shape of the 11-bit-digit sort's scatter kernel
+    int pdl;                 // 1: the plan and scatter kernels launch as programmatic dependents
 };
 Knobs& knobs();
 // Whether a typed sort of n items launches two instances of every scatter
@@ -240,6 +242,26 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
                                  uint32_t key_type = 0);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Launch `kern` on `stream`; with knobs().pdl set, as a programmatic
+// dependent of the kernel before it on the stream, so that it becomes
+// resident while that kernel finishes (the kernel calls pdl_wait() before
+// reading that kernel's output).
+template <typename... Params, typename... Args>
+cudaError_t launch_after_previous(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t stream, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = knobs().pdl ? 1u : 0u;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // One bit per device (ordinal < 64) for one-time host setup of a kernel
 // (its shared-memory limit), safe when several host threads enqueue sorts.

@@ -184,6 +184,10 @@ k_onesweep(K* __restrict__ ka, V* __restrict__ va,
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+    // The plan, the histograms' status clearing and the pass before this
+    // one are all complete from here on.
+    pdl_launch_next();
+    pdl_wait();
     if (key_type & (ROLE_PLAIN_PASSES | ROLE_MAP_PASSES)) {
         // One of the two instances of a typed sort's pass: keep the pass if
         // it is this instance's (an executed first or last pass needs the

@@ -49,12 +49,12 @@ static rs_status launch_onesweep_shape(K* ka, V* va, K* kb, V* vb,
     if (grid > tiles) grid = tiles;
     if (grid == 0) return RS_OK;
     note_launch_begin(SEG ? KK_SEG_ONESWEEP : KK_ONESWEEP, stream);
-    kern<<<grid, THREADS, L::BYTES, stream>>>(ka, va, kb, vb, n, pass, slot, tiles, ctrl, sticky,
-                                              static_cast<S*>(status), static_cast<S*>(status_clear),
-                                              tiles * RADIX, knobs().spin_limit, knobs().debug,
-                                              seg.tile_geo, seg.gofs, key_type);
+    const cudaError_t e = launch_after_previous(
+        kern, dim3(grid), dim3(THREADS), L::BYTES, stream, ka, va, kb, vb, n, pass, slot, tiles,
+        ctrl, sticky, static_cast<S*>(status), static_cast<S*>(status_clear), tiles * RADIX,
+        knobs().spin_limit, knobs().debug, seg.tile_geo, seg.gofs, key_type);
     note_launch_end(SEG ? KK_SEG_ONESWEEP : KK_ONESWEEP, stream);
-    return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+    return e == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
 template <bool PAIRS, typename S, bool SEG>

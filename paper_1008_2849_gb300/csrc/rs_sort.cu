@@ -176,10 +176,12 @@ rs_status enqueue_sort(uint32_t* keys, uint32_t* vals, uint32_t n, cudaStream_t 
     st = enqueue_hist4(keys, n, &ctrl->hist[0][0], status[0], status_bytes, key_type, stream);
     if (st != RS_OK) return st;
     note_launch_begin(KK_PLAN, stream);
-    k_plan<PASSES><<<1, 1024, 0, stream>>>(ctrl, n, msd ? 1u : 0u, warp_max, small_sort_capacity(),
-                                   msd_off, msd_tiny, msd_small);
+    const cudaError_t pe = launch_after_previous(k_plan<PASSES>, dim3(1), dim3(1024), 0, stream,
+                                                 ctrl, n, msd ? 1u : 0u, warp_max,
+                                                 small_sort_capacity(), msd_off, msd_tiny,
+                                                 msd_small);
     note_launch_end(KK_PLAN, stream);
-    if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
+    if (pe != cudaSuccess) return RS_ERR_CUDA;
 
     const int cfg = pairs ? ck.tile_pairs : ck.tile_keys;
     if (msd) {

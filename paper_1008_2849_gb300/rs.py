@@ -488,7 +488,7 @@ def profile_read() -> dict:
 
 TUNE_KNOBS = {"tile_pairs": 0, "tile_keys": 1, "hist_ctas_per_sm": 2, "hist_mode": 3,
               "small_max": 4, "tile_seg": 5, "warp_max": 6, "small_bits": 7, "msd": 8,
-              "typed_split": 9, "d11_shape": 10, "digits": 11}
+              "typed_split": 9, "d11_shape": 10, "digits": 11, "pdl": 13}
 
 
 def tune_set(knob: str, value: int) -> None:
