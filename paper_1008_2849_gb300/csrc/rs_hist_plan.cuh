@@ -142,13 +142,24 @@ k_hist4_cols(const uint32_t* __restrict__ keys, uint32_t n, uint32_t* __restrict
         for (uint32_t p = 0; p < PASSES; ++p)
             atomicAdd(mycol + ((p * RADIX + ((key >> (p * RADIX_BITS)) & (RADIX - 1))) << 5), 1u);
     };
-    // Two independent 16-byte loads in flight per thread and iteration.
-    for (uint32_t i = gtid; i < body4; i += 2 * gsize) {
-        const uint4 v0 = ld_stream(body + i);
-        const bool has1 = i + gsize < body4;
-        const uint4 v1 = has1 ? ld_stream(body + i + gsize) : make_uint4(0, 0, 0, 0);
-        count_key(v0.x); count_key(v0.y); count_key(v0.z); count_key(v0.w);
-        if (has1) { count_key(v1.x); count_key(v1.y); count_key(v1.z); count_key(v1.w); }
+    // HIST_LOADS independent 16-byte loads in flight per thread and
+    // iteration (64 KiB per SM): enough bytes in flight to cover the HBM
+    // latency at full bandwidth.
+    constexpr uint32_t HIST_LOADS = 4;
+    for (uint32_t i = gtid; i < body4; i += HIST_LOADS * gsize) {
+        uint4 v[HIST_LOADS];
+#pragma unroll
+        for (uint32_t u = 0; u < HIST_LOADS; ++u)
+            v[u] = i + u * gsize < body4 ? ld_stream(body + i + u * gsize) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (uint32_t u = 0; u < HIST_LOADS; ++u) {
+            if (i + u * gsize < body4) {
+                count_key(v[u].x);
+                count_key(v[u].y);
+                count_key(v[u].z);
+                count_key(v[u].w);
+            }
+        }
     }
     if (blockIdx.x == 0 && tid < 8) {
         const uint32_t i = tid < 4 ? tid : tail + (tid - 4);
