@@ -25,20 +25,42 @@ def test_size_classes(rs):
 def test_apply_table_and_restore(rs, tmp_path):
     from paper_1008_2849_gb300 import autotune
     saved = {(c, k): rs.tune_get_class(c, k) for c in range(6)
-             for k in ("tile_pairs", "tile_keys", "tile_seg", "small_max")}
+             for k in ("tile_pairs", "tile_keys", "tile_seg", "small_max", "digits")}
     try:
         table = {"device": "test", "classes": {"2": {"tile_pairs": 1, "tile_keys": 2},
-                                               "4": {"tile_seg": 5, "small_max": 8192}}}
+                                               "4": {"tile_seg": 5, "small_max": 8192,
+                                                     "digits": 11}}}
         p = tmp_path / "t.json"
         p.write_text(json.dumps(table))
         autotune.apply(autotune.load(str(p)))
         assert rs.tune_get_class(2, "tile_pairs") == 1 and rs.tune_get_class(2, "tile_keys") == 2
         assert rs.tune_get_class(4, "tile_seg") == 5 and rs.tune_get_class(4, "small_max") == 8192
+        assert rs.tune_get_class(4, "digits") == 11 and rs.tune_get_class(3, "digits") == 8
         assert rs.tune_get_class(3, "tile_pairs") == saved[(3, "tile_pairs")]
         with pytest.raises(rs.RsError):
             rs.tune_set_class(0, "tile_pairs", 99)
         with pytest.raises(rs.RsError):
             rs.tune_set_class(7, "tile_pairs", 0)
+    finally:
+        for (c, k), v in saved.items():
+            rs.tune_set_class(c, k, v)
+
+
+def test_committed_table_applies(rs):
+    """The measured GB300 table loads and applies; it keeps 8-bit digits and
+    the one-CTA sort limits within range."""
+    import os
+    from paper_1008_2849_gb300 import autotune
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    table = autotune.load(os.path.join(root, "paper_1008_2849_gb300", "tuning_gb300.json"))
+    saved = {(c, k): rs.tune_get_class(c, k) for c in range(6)
+             for k in ("tile_pairs", "tile_keys", "tile_seg", "small_max", "warp_max",
+                       "small_bits", "msd", "digits")}
+    try:
+        autotune.apply(table)
+        for c in range(6):
+            assert rs.tune_get_class(c, "digits") == 8
+            assert 0 <= rs.tune_get_class(c, "small_max") <= 8192
     finally:
         for (c, k), v in saved.items():
             rs.tune_set_class(c, k, v)
