@@ -316,6 +316,7 @@ k_hist8(const unsigned long long* __restrict__ keys, uint32_t n, uint32_t* __res
         uint4* __restrict__ clear, uint32_t clear_vec4, uint32_t key_type) {
     __shared__ uint32_t s_h[PASSES64 * RADIX];
     const uint32_t tid = threadIdx.x;
+    pdl_launch_next();  // the plan kernel may launch; it waits for this one
     for (uint32_t i = tid; i < PASSES64 * RADIX; i += THREADS) s_h[i] = 0;
     const uint32_t gtid = blockIdx.x * THREADS + tid;
     const uint32_t gsize = gridDim.x * THREADS;

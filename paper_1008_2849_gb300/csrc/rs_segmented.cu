@@ -103,15 +103,20 @@ rs_status enqueue_sort_segmented(uint32_t* keys, uint32_t* vals, uint32_t n,
         static DeviceOnce smem_set[2];
         st = allow_smem_once(kern, SMEM, smem_set[key_type != KEY_U32 ? 1 : 0]);
         if (st != RS_OK) return st;
-        kern<<<di.sm_count, SEG_HIST_THREADS, SMEM, stream>>>(
-            keys, ctrl, tile_geo, gofs, static_cast<uint4*>(status[0]),
-            (uint32_t)((L.status1 - L.status0) / sizeof(uint4)), key_type);
+        if (launch_after_previous(kern, dim3(di.sm_count), dim3(SEG_HIST_THREADS), SMEM, stream,
+                                  (const uint32_t*)keys, (const Ctrl*)ctrl,
+                                  (const uint4*)tile_geo, gofs, static_cast<uint4*>(status[0]),
+                                  (uint32_t)((L.status1 - L.status0) / sizeof(uint4)),
+                                  key_type) != cudaSuccess)
+            return RS_ERR_CUDA;
     }
     note_launch_end(KK_SEG_HIST, stream);
     note_launch_begin(KK_SEG_SCAN, stream);
-    k_seg_scan<PASSES><<<di.sm_count * 2, 1024, 0, stream>>>(ctrl, gofs, large_first);
+    const cudaError_t se = launch_after_previous(k_seg_scan<PASSES>, dim3(di.sm_count * 2),
+                                                 dim3(1024), 0, stream, (const Ctrl*)ctrl, gofs,
+                                                 (const uint32_t*)large_first);
     note_launch_end(KK_SEG_SCAN, stream);
-    if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
+    if (se != cudaSuccess) return RS_ERR_CUDA;
 
     SegView view;
     view.tile_geo = tile_geo;

@@ -41,6 +41,8 @@ k_seg_plan(const uint32_t* __restrict__ off, uint32_t num_segments, uint32_t n, 
            uint32_t npass = PASSES) {
     __shared__ uint32_t s_carry[2];  // tiles and large segments before this chunk
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    pdl_launch_next();
+    pdl_wait();
 
     bool bad = false;
     for (uint32_t s = tid; s < num_segments; s += 1024) {
@@ -133,6 +135,8 @@ k_seg_hist(const uint32_t* __restrict__ keys, const Ctrl* __restrict__ ctrl,
     uint32_t* const s_col = reinterpret_cast<uint32_t*>(s_cols4);
     constexpr uint32_t T = SEG_HIST_THREADS;
     const uint32_t tid = threadIdx.x, lane = tid & 31;
+    pdl_launch_next();
+    pdl_wait();  // the planner and the on-chip sorts are complete
     for (uint32_t i = blockIdx.x * T + tid; i < clear_vec4; i += gridDim.x * T)
         clear[i] = make_uint4(0, 0, 0, 0);
     if (ctrl->err != 0) return;
@@ -229,6 +233,8 @@ k_seg_scan(const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ hist,
     __shared__ uint32_t s_warp[32];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = tid >> 8;
+    pdl_launch_next();
+    pdl_wait();  // the segment histograms are complete
     if (ctrl->err != 0) return;
     const uint32_t large = ctrl->large_count;
     for (uint32_t g = blockIdx.x; g < large; g += gridDim.x)

@@ -21,10 +21,11 @@ rs_status launch_small_shape(uint32_t* keys, uint32_t* vals, const uint32_t* src
     rs_status st = allow_smem_once(kern, SMEM, smem_set);
     if (st != RS_OK) return st;
     note_launch_begin(KK_SMALL, stream);
-    kern<<<grid, THREADS, SMEM, stream>>>(keys, vals, src_keys, src_vals, off, list, ctrl, single_n,
-                                          key_type);
+    const cudaError_t e = launch_after_previous(kern, dim3(grid), dim3(THREADS), SMEM, stream, keys,
+                                                vals, src_keys, src_vals, off, list, ctrl,
+                                                single_n, key_type);
     note_launch_end(KK_SMALL, stream);
-    return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+    return e == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
 template <int BITS, bool PAIRS>
@@ -51,10 +52,11 @@ rs_status launch_warp_bits(uint32_t* keys, uint32_t* vals, const uint32_t* src_k
     rs_status st = allow_smem_once(kern, L::BYTES, smem_set);
     if (st != RS_OK) return st;
     note_launch_begin(KK_WARP, stream);
-    kern<<<grid, WARP_SORT_THREADS, L::BYTES, stream>>>(keys, vals, src_keys, src_vals, off, list,
-                                                         ctrl, single_n, key_type);
+    const cudaError_t e =
+        launch_after_previous(kern, dim3(grid), dim3(WARP_SORT_THREADS), L::BYTES, stream, keys,
+                              vals, src_keys, src_vals, off, list, ctrl, single_n, key_type);
     note_launch_end(KK_WARP, stream);
-    return cudaPeekAtLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+    return e == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
 }  // namespace

@@ -52,6 +52,8 @@ k_warp_sort(uint32_t* keys, uint32_t* vals, const uint32_t* src_keys, const uint
             const uint32_t* __restrict__ off, const uint32_t* __restrict__ list,
             const Ctrl* __restrict__ ctrl, uint32_t single_n, uint32_t key_type) {
     using L = WarpSortSmem<ITEMS, BITS, PAIRS>;
+    pdl_launch_next();
+    pdl_wait();  // the kernel before this one (planner, MSD pass) is complete
     constexpr uint32_t NB = 1u << BITS;
     constexpr uint32_t NPASS = 32 / BITS;
     constexpr uint32_t CAP = L::CAP;
@@ -174,6 +176,8 @@ k_small_sort(uint32_t* keys, uint32_t* vals, const uint32_t* src_keys, const uin
     constexpr uint32_t CAP = THREADS * ITEMS;
     constexpr uint32_t WARP_ITEMS = 32 * ITEMS;
     static_assert(THREADS >= (int)NB && 32 % BITS == 0, "one thread per digit, whole passes");
+    pdl_launch_next();
+    pdl_wait();  // the kernel before this one (planner, MSD pass) is complete
     extern __shared__ uint4 s_dyn[];
     uint32_t* const s_k = reinterpret_cast<uint32_t*>(s_dyn);  // [2][CAP]
     uint32_t* const s_v = s_k + 2 * CAP;                       // [2][CAP] (pairs)

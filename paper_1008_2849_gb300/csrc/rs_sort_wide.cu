@@ -124,12 +124,14 @@ rs_status enqueue_sort_wide(void* keys, void* vals, uint32_t n, uint32_t key_typ
         if (st != RS_OK) return st;
     }
     note_launch_begin(KK_PLAN, stream);
-    if (key64)
-        k_plan<PASSES64><<<1, 1024, 0, stream>>>(ctrl, n, 0u, 0u, 0u, nullptr, nullptr, nullptr);
-    else
-        k_plan<PASSES><<<1, 1024, 0, stream>>>(ctrl, n, 0u, 0u, 0u, nullptr, nullptr, nullptr);
+    uint32_t* const no_list = nullptr;
+    const cudaError_t pe =
+        key64 ? launch_after_previous(k_plan<PASSES64>, dim3(1), dim3(1024), 0, stream, ctrl, n,
+                                      0u, 0u, 0u, no_list, no_list, no_list)
+              : launch_after_previous(k_plan<PASSES>, dim3(1), dim3(1024), 0, stream, ctrl, n, 0u,
+                                      0u, 0u, no_list, no_list, no_list);
     note_launch_end(KK_PLAN, stream);
-    if (cudaPeekAtLastError() != cudaSuccess) return RS_ERR_CUDA;
+    if (pe != cudaSuccess) return RS_ERR_CUDA;
 
     for (uint32_t p = 0; p < npass; ++p) {
         void* cur = status[p & 1];
