@@ -180,16 +180,16 @@ rs_status check_sort_args(const uint32_t* keys, const uint32_t* vals, size_t n) 
 Knobs& knobs() {
     // Defaults chosen by the autotuner on GB300 (tuning_gb300.json): arrays up
     // to 8192 items take the one-CTA sort; up to 2^20 items tile shape 1
-    // (512 x 8, two CTAs per SM; key-value arrays up to 2^16: shape 4, 384 x
-    // 12); larger ones shape 3 (384 x 13, two CTAs per SM), and for keys only
-    // shape 6 (384 x 18: no value buffer, still two CTAs).
+    // (512 x 8, two CTAs per SM); larger ones shape 3 (384 x 13, two CTAs per
+    // SM), and for keys only shape 6 (384 x 18: no value buffer, still two
+    // CTAs).
     // Per class:
     // {tile_pairs, tile_keys, tile_seg, small_max, warp_max, small_bits, msd,
     //  digits}.
     // The MSD-first order measured faster only up to 2^16 items (class 1).
     // The 11-bit-digit order (three passes) measured slower in every class
     // (2.3 to 2.8 times the 8-bit sort at 2^24 to 2^28 pairs), so it is off.
-    static Knobs k{{{1, 1, 3, 8192, 512, 8, 0, 8}, {4, 1, 3, 4096, 512, 8, 1, 8},
+    static Knobs k{{{1, 1, 3, 8192, 512, 8, 0, 8}, {1, 1, 3, 4096, 512, 8, 1, 8},
                     {1, 1, 3, 4096, 512, 8, 0, 8}, {3, 6, 3, 4096, 512, 8, 0, 8},
                     {3, 6, 3, 4096, 512, 8, 0, 8}, {3, 6, 3, 4096, 512, 8, 0, 8}},
                    kDefaultSpinLimit, 0, 4, 3, kDefaultTypedSplitMin, 1, 1};
